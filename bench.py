@@ -1,0 +1,342 @@
+"""Benchmark: FP64 cell-updates per second per RK stage of the GB300 Euler solver.
+
+Workload (the metric's configuration): 2D Euler, Kelvin-Helmholtz shear layer
+on a periodic 4096 x 4096 grid, FP64, MUSCL-minmod + Roe flux + SSP-RK3 with
+CFL 0.5.  One bench step is one SSP-RK3 time step (CFL time-step reduction +
+three fused stage kernels), replayed from a CUDA graph by fv_run; the state
+keeps evolving across steps as in the 200-step run.
+  value = cells * 3 stages * steps / device time (CUDA events, max over ranks)
+  e2e   = the same through fv_run with a pinned HOST state: every step copies
+          the state in, advances it and copies it back.
+The state (537 MB) is larger than L2 (129 MB), so no flush is needed.
+
+--impl reference times the CPU oracle (the only reference this paper has; it
+ships no code) on the host cores, on a bounded band of the same workload.
+Multi-GPU: the method does not shard here; N ranks run N independent replicas
+(weak scaling), value = all ranks' cell-stages / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_CELLS_SIDE = 4096
+METRIC = "FP64 cell-updates/s per RK stage (2D Euler KH 4096^2, MUSCL-minmod + Roe + SSP-RK3)"
+UNIT = "cell-stage/s"
+# Algorithmic FP64 work per cell and RK stage, counted on the CPU oracle with an
+# operation-counting scalar (python -m oracle.count_flops; 2D value at n = 4096):
+# every +, -, *, /, sqrt of the plain method counts one FLOP.
+FLOP_PER_CELL_STAGE_2D = 496.44
+# Algorithmic HBM bytes per cell-stage: stage 1 reads U^n and writes U^1 (4+4
+# doubles), stages 2 and 3 read U^s and U^n and write (12 doubles): 256 B per
+# cell and step over 3 stages.
+BYTES_PER_CELL_STAGE_2D = 256.0 / 3.0
+# FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz
+# (a DFMA loop measured 1.18 TFLOP/s on this part).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM traffic of one stage-kernel launch from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, full 4096^2 launch), valid for the kernel sources
+# whose hash is recorded with it; null otherwise.
+STAGE_TRAFFIC = {"bytes": None, "source_hash": None}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("fv_stage.cuh", "fv_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2306_14011_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.path = None
+        if shutil.which("nvidia-smi") is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id is not None:
+            cmd += ["-i", str(gpu_id)]
+        self.out = open(self.path, "w")
+        self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("[N/A]", ""))}
+
+
+def gpu_uuid(torch):
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        return dist, rank, world
+    return None, rank, world
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2306_14011_gb300 import fv
+    from paper_2306_14011_gb300 import inputs as I
+
+    dist, rank, world = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.n
+    g, U0 = I.kelvin_helmholtz(n, seed=1)
+    cells = g.ncells
+    stream = torch.cuda.current_stream()
+    solver = fv.Solver(g, stream=stream)
+    U = torch.from_numpy(U0).to(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up: untimed steps (first call captures the graphs)
+    solver.run(U, args.warmup)
+    barrier()
+
+    clocks = ClockSampler(gpu_uuid(torch))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    solver.run(U, args.steps)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t_dev = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t_dev, op=dist.ReduceOp.MAX)
+    ms_max = t_dev.item()
+    solver.sync()  # reports non-physical / timeout flags of the timed region
+
+    # dominant kernel (fused stage kernel): average launch duration over the
+    # timed region = (timed region - K x the time-step reduction) / (3 K); the
+    # reduction (memset + dt kernel) is timed alone with CUDA events right after.
+    dtbuf = torch.zeros(1, dtype=torch.float64, device=dev)
+    reps = max(3, min(args.steps, 20))
+    fv.fv_time_step(solver.ctx, U, dtbuf)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(reps):
+        fv.fv_time_step(solver.ctx, U, dtbuf)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    dt_ms = e2.elapsed_time(e3) / reps
+    stage_ms = (ms - args.steps * dt_ms) / (3 * args.steps)
+
+    # end to end through the C ABI with a pinned host state
+    e2e = None
+    if args.e2e_steps > 0:
+        Uh_t = torch.from_numpy(U.cpu().numpy()).pin_memory()
+        Uh = Uh_t.numpy()
+        solver.run(Uh, 1)  # warm (allocates the staging buffers, captures graphs)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            solver.run(Uh, 1)  # H2D copy, one SSP-RK3 step, D2H copy, wait
+        t1 = time.perf_counter()
+        tt = torch.tensor([t1 - t0], dtype=torch.float64, device=dev)
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * cells * 3 * args.e2e_steps / tt.item(), "unit": UNIT,
+               "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(U0.nbytes),
+               "steps": args.e2e_steps}
+
+    if rank != 0:
+        solver.close()
+        return None
+
+    value = world * cells * 3 * args.steps / (ms_max / 1e3)
+    flops_per_launch = FLOP_PER_CELL_STAGE_2D * cells
+    achieved_tflops = flops_per_launch / (stage_ms / 1e3) / 1e12
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    achieved_gbs = BYTES_PER_CELL_STAGE_2D * cells / (stage_ms / 1e3) / 1e9
+    traffic = STAGE_TRAFFIC["bytes"] if STAGE_TRAFFIC["source_hash"] == kernel_source_hash() else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded Kelvin-Helmholtz initial condition)",
+        "config": {"workload": f"2D Euler Kelvin-Helmholtz {n}x{n} periodic, FP64, MUSCL-minmod + Roe + SSP-RK3, "
+                               f"CFL 0.5; 1 bench step = 1 SSP-RK3 step (dt reduction + 3 fused stage kernels) "
+                               f"replayed from a CUDA graph",
+                   "cells": cells, "launch": "default", "launch_params": solver.launch,
+                   "l2": "state (%.0f MB) larger than L2, no flush" % (U0.nbytes / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "fvk::stage_kernel<2, stage>", "stage_ms": stage_ms, "dt_kernel_ms": dt_ms,
+                     "flop_per_cell_stage": FLOP_PER_CELL_STAGE_2D,
+                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz",
+                     "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": (achieved_gbs / hbm_peak) if hbm_peak else None,
+                     "bytes_per_cell_stage": BYTES_PER_CELL_STAGE_2D},
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+        "impl": "ours",
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args, U0, g)
+    solver.close()
+    return line
+
+
+def _band(U0, g, rows):
+    """A band of `rows` rows of the workload state, periodic in x and
+    transmissive at the band's y edges (same per-cell work as the full grid)."""
+    from paper_2306_14011_gb300 import inputs as I
+    n = g.n[0]
+    y0 = (g.n[1] - rows) // 2
+    gb = I.GridSpec(2, (n, rows, 1), (g.length[0], g.length[1] * rows / g.n[1], 1.0),
+                    ((I.BC_PERIODIC, I.BC_PERIODIC), (I.BC_TRANSMISSIVE, I.BC_TRANSMISSIVE),
+                     (I.BC_PERIODIC, I.BC_PERIODIC)))
+    return gb, np.ascontiguousarray(U0[:, y0:y0 + rows, :])
+
+
+def cpu_baseline(args, U0, g):
+    """The oracle as it stands, on the host cores, for ~10-30 s of CPU work:
+    SSP-RK3 steps of a 1024-row band of the workload."""
+    from oracle import oracle as O
+    gb, Ub = _band(U0, g, args.cpu_rows)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        Ub, _ = O.run(gb, Ub, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= args.cpu_seconds or steps >= 50:
+            break
+    return {"value": gb.ncells * 3 * steps / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 step(s) of the C++ oracle on a {gb.n[0]}x{gb.n[1]} band of the "
+                      f"{g.n[0]}x{g.n[1]} KH state ({el:.1f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    from paper_2306_14011_gb300 import inputs as I
+    g, U0 = I.kelvin_helmholtz(args.n, seed=1)
+    gb, Ub = _band(U0, g, args.ref_rows)
+    for _ in range(args.warmup):
+        Ub, _ = O.run(gb, Ub, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Ub, _ = O.run(gb, Ub, 1)
+    el = time.perf_counter() - t0
+    value = gb.ncells * 3 * args.steps / el
+    sample = (f"each step: one SSP-RK3 step of the C++ oracle on a {gb.n[0]}x{gb.n[1]} band of the "
+              f"{g.n[0]}x{g.n[1]} KH state")
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Kelvin-Helmholtz initial condition)",
+        "config": {"workload": f"2D Euler Kelvin-Helmholtz {g.n[0]}x{g.n[1]} periodic, FP64 (CPU oracle, "
+                               f"{gb.n[1]}-row band per step)", "cells": gb.ncells},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=N_CELLS_SIDE, help="grid cells per side (default: the workload's 4096)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-rows", type=int, default=1024)
+    ap.add_argument("--ref-rows", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

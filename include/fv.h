@@ -1,0 +1,163 @@
+/*
+ * libfv: FP64 structured-grid Euler solver for GB300 (sm_103a), C ABI.
+ *
+ * The library advances the semi-discrete finite-volume form of the Euler
+ * equations,   |Omega_k| dU/dt + R_h(U) = 0          (paper Eq. (4)),
+ * with the spatial residual of Eq. (5) (source term S = 0),
+ *              R_h = sum over the cell's faces of F.n ds,
+ * face states from the MUSCL extrapolation of conserved variables, Eq. (6),
+ * with the minmod limiter, and F the Roe approximate-Riemann flux with
+ * Harten's entropy fix on the acoustic waves (the paper names neither flux nor
+ * limiter; these are the pinned readings).  Time marching is the three-stage
+ * SSP Runge-Kutta scheme (the paper: "an explicit Runge-Kutta time marching
+ * method", Sec. 3.2) with a CFL time step.
+ *
+ * Data layout (struct of arrays, the SoA layout of Sec. 3.1): a state is
+ * float64, contiguous, U[v][z][y][x] with x fastest; v = 0..nvar-1 indexes
+ * (rho, rho*u, rho*v[, rho*w], rho*e_t); nvar = 4 in 2D and 5 in 3D.  Only
+ * interior cells are stored: ghost cells are generated inside the kernels
+ * from the boundary conditions.
+ *
+ * Pointers.  State and residual arrays may be device pointers (used in place,
+ * stream-ordered on the context's stream, the call returns without waiting)
+ * or host pointers (the call copies them to the device and back through a
+ * staging buffer owned by the context and waits for the copies).  The caller
+ * owns every array it passes; the context owns its workspaces.
+ *
+ * Errors.  Every call returns an fv_status.  Argument errors are detected on
+ * the host before anything is launched.  Device-side conditions (a cell with
+ * rho <= 0, p <= 0 or a NaN seen by the time-step kernel; a bounded wait that
+ * ran out) set flags in device memory that are reported by the next call that
+ * waits for the device (fv_sync, or any call given a host output pointer).
+ * No call aborts the process or throws.
+ */
+#ifndef FV_H
+#define FV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fv_status {
+  FV_OK = 0,
+  FV_EINVAL = 1,         /* an argument is out of range or inconsistent */
+  FV_ENOMEM = 2,         /* device or host allocation failed */
+  FV_ECUDA = 3,          /* a CUDA runtime or driver call failed */
+  FV_ENONPHYSICAL = 4,   /* a cell had rho <= 0, p <= 0 or a NaN */
+  FV_ETIMEOUT = 5,       /* a bounded device-side wait gave up */
+  FV_EUNSUPPORTED = 6    /* valid request this build does not implement */
+} fv_status;
+
+enum { FV_BC_PERIODIC = 0, FV_BC_TRANSMISSIVE = 1 };
+
+/* A uniform Cartesian single-block grid: dim = 2 or 3, n = cells per axis
+ * (n[2] = 1 in 2D), len = domain extent per axis (spacing len/n), bc = per
+ * axis (low, high) FV_BC_PERIODIC (must be set on both sides) or
+ * FV_BC_TRANSMISSIVE (zero-gradient ghost cells). */
+typedef struct fv_grid {
+  int dim;
+  int n[3];
+  double len[3];
+  int bc[3][2];
+} fv_grid;
+
+/* gamma: ratio of specific heats (1.4).  cfl: CFL number (0.5).
+ * eps, kappa: MUSCL parameters of Eq. (6); eps = 1 gives second order; with
+ * the minmod limiter the two kappa-weighted limited slopes are equal, so
+ * kappa has no effect on the result (accepted for completeness).
+ * efix: Harten entropy-fix width as a fraction of the Roe sound speed (0.1);
+ * 0 disables the fix. */
+typedef struct fv_scheme {
+  double gamma, cfl, eps, kappa, efix;
+} fv_scheme;
+
+enum { FV_LOADER_TMA = 0, FV_LOADER_PLAIN = 1 };
+
+/* Launch parameters of one kernel: the tunables of the autotuner.
+ * Tiled kernels (residual and RK stages): cells per CTA tile (tile[0] even,
+ * 2..252 per axis, tile[2] = 1 in 2D), threads per CTA (32..256, a multiple
+ * of 32); grid must be 0 (one CTA per tile covers the domain); loader
+ * FV_LOADER_TMA stages tiles with TMA when the grid allows it (even nx, a
+ * 16-byte aligned state, tile + halo no larger than the grid) and falls back
+ * to plain loads otherwise, FV_LOADER_PLAIN always uses plain loads.
+ * Time-step reduction: threads per CTA (32..1024) and grid = number of CTAs
+ * (0 = two per SM); tile and loader are ignored. */
+typedef struct fv_kernel_cfg {
+  int tile[3];
+  int threads;
+  int grid;
+  int loader;
+} fv_kernel_cfg;
+
+/* stage[s]: RK stage s+1 (fv_residual uses stage[0]); dt: time-step reduction. */
+typedef struct fv_launch {
+  fv_kernel_cfg stage[3];
+  fv_kernel_cfg dt;
+} fv_launch;
+
+typedef struct fv_ctx fv_ctx;
+
+/* Fill *l with the default launch configuration for grid g (one tile shape
+ * and thread count for all stages).  Returns FV_EINVAL for a bad grid. */
+int fv_default_launch(const fv_grid *g, fv_launch *l);
+
+/* Create a solver context for ngrids grids (ngrids = 1; batched grids return
+ * FV_EUNSUPPORTED).  Allocates the RK stage buffers and reduction scratch on
+ * the current CUDA device.  stream: a cudaStream_t on which every later call
+ * is ordered (NULL = the legacy default stream).  l = NULL selects
+ * fv_default_launch.  On success *out owns the context (free with
+ * fv_destroy). */
+int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, const fv_launch *l,
+            void *stream);
+
+/* Replace / read the launch configuration (validated against the device). */
+int fv_set_launch(fv_ctx *ctx, const fv_launch *l);
+int fv_get_launch(const fv_ctx *ctx, fv_launch *l);
+
+/* Spatial residual R_h of Eq. (5): R = sum over faces of F.n ds, face areas
+ * included (not divided by |Omega|).  U, R: nvar*ncells doubles (R may not
+ * alias U).  rnorm2: NULL, or nvar doubles (device or host) receiving
+ * sum over cells of R_v^2 per conserved variable. */
+int fv_residual(fv_ctx *ctx, const double *U, double *R, double *rnorm2);
+
+/* CFL time step dt = cfl / max over cells of sum_d (|u_d| + c) / dx_d.
+ * dt_out: a host pointer (the call waits) or a device pointer (written
+ * stream-ordered).  Non-physical cells make the call return FV_ENONPHYSICAL
+ * when dt_out is a host pointer. */
+int fv_time_step(fv_ctx *ctx, const double *U, double *dt_out);
+
+/* One SSP-RK3 step applied in place to U:
+ *   U1 = U + dt L(U),  U2 = 3/4 U + 1/4 (U1 + dt L(U1)),
+ *   U <- 1/3 U + 2/3 (U2 + dt L(U2)),   L(U) = -R_h(U) / |Omega|.
+ * dt > 0 is used as given; dt <= 0 takes the CFL step of U.  dt_used: NULL or
+ * a host pointer that receives the step taken (the call then waits). */
+int fv_rk_step(fv_ctx *ctx, double *U, double dt, double *dt_used);
+
+/* nsteps SSP-RK3 steps in place, replayed from CUDA graphs captured on the
+ * first call for this U pointer and dt mode.  dt_fixed > 0 holds the step;
+ * otherwise every step takes the CFL step of its starting state.  t_out:
+ * NULL (asynchronous) or a host pointer receiving the simulated time (the
+ * call waits and reports device-side flags). */
+int fv_run(fv_ctx *ctx, double *U, int nsteps, double dt_fixed, double *t_out);
+
+/* Wait for all work of the context and report (then clear) device-side
+ * flags: FV_ENONPHYSICAL, FV_ETIMEOUT, or FV_OK. */
+int fv_sync(fv_ctx *ctx);
+
+/* Free the context and its device memory (waits for its work first). */
+void fv_destroy(fv_ctx *ctx);
+
+/* Static description of a status code. */
+const char *fv_strerror(int status);
+
+/* Diagnostic of the device arithmetic used by the kernels: for n inputs x
+ * (device pointer), out_rsqrt[i] = 1/sqrt(x[i]) and out_rcp[i] = 1/x[i] as
+ * computed inside the flux kernels (approximation refined to full double
+ * precision).  Stream-ordered on `stream`. */
+int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FV_H */

@@ -4,6 +4,9 @@
 #include "fv_oracle.hpp"
 
 #include <atomic>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace orc {
 
@@ -66,6 +69,19 @@ int orc_residual(const Grid *g, const Scheme *s, const double *U, double *R) {
   return 0;
 }
 
+// The residual evaluated in extended precision (long double: 64-bit or
+// 113-bit significand depending on the host) from the same double inputs,
+// for measuring the rounding error of FP64 evaluations.
+int orc_residual_ext(const Grid *g, const Scheme *s, const double *U, double *R) {
+  Layout L(*g);
+  size_t N = L.cells() * L.nv;
+  std::vector<long double> X(N), Y(N);
+  for (size_t c = 0; c < N; ++c) X[c] = U[c];
+  residual(*g, *s, X.data(), Y.data());
+  for (size_t c = 0; c < N; ++c) R[c] = (double)Y[c];
+  return 0;
+}
+
 // CFL time step; -1 when a cell is non-physical.
 double orc_time_step(const Grid *g, const Scheme *s, const double *U) { return time_step(*g, *s, U); }
 
@@ -95,25 +111,28 @@ double orc_run(const Grid *g, const Scheme *s, double *U, int nsteps, double dt_
   return t;
 }
 
+}  // extern "C"
+
 // Residual of a list of cells only (flat interior indices k*ny*nx + j*nx + i),
 // for sampled checks on grids too large for the full oracle.  out: [ncells][nv].
-int orc_residual_cells(const Grid *g, const Scheme *s, const double *U, long ncells, const long *cells, double *out) {
+template <class T>
+void residual_cells(const Grid *g, const Scheme *s, const double *U, long ncells, const long *cells, double *out) {
   Layout L(*g);
   const int nv = L.nv;
 #pragma omp parallel for schedule(dynamic, 64)
   for (long c = 0; c < ncells; ++c) {
     long id = cells[c];
     int i = (int)(id % L.n[0]), j = (int)((id / L.n[0]) % L.n[1]), k = (int)(id / ((long)L.n[0] * L.n[1]));
-    double R[5] = {0, 0, 0, 0, 0};
+    T R[5] = {T(0), T(0), T(0), T(0), T(0)};
     for (int d = 0; d < L.dim; ++d) {
       double ds = 1.0;
       for (int a = 0; a < L.dim; ++a)
         if (a != d) ds *= L.h[a];
-      double Fside[2][5];
+      T Fside[2][5];
       for (int side = 0; side < 2; ++side) {  // face k-1/2 then k+1/2
-        double QL[5], QR[5];
+        T QL[5], QR[5];
         for (int v = 0; v < nv; ++v) {
-          double q[4];
+          T q[4];
           for (int t = 0; t < 4; ++t) {
             int c3[3] = {i, j, k};
             c3[d] += side + t - 2;  // cells k-2+side .. k+1+side
@@ -128,8 +147,21 @@ int orc_residual_cells(const Grid *g, const Scheme *s, const double *U, long nce
       }
       for (int v = 0; v < nv; ++v) R[v] += (Fside[1][v] - Fside[0][v]) * ds;
     }
-    for (int v = 0; v < nv; ++v) out[c * nv + v] = R[v];
+    for (int v = 0; v < nv; ++v) out[c * nv + v] = (double)R[v];
   }
+}
+
+extern "C" {
+
+int orc_residual_cells(const Grid *g, const Scheme *s, const double *U, long ncells, const long *cells, double *out) {
+  residual_cells<double>(g, s, U, ncells, cells, out);
+  return 0;
+}
+
+// The same in extended precision (long double), rounded to double at the end.
+int orc_residual_cells_ext(const Grid *g, const Scheme *s, const double *U, long ncells, const long *cells,
+                           double *out) {
+  residual_cells<long double>(g, s, U, ncells, cells, out);
   return 0;
 }
 
@@ -187,6 +219,15 @@ int orc_count_ops(const Grid *g, const Scheme *s, const double *U, double dt, lo
   rk3_step(*g, *s, X.data(), dt);
   grab(counts + 8);
   return 0;
+}
+
+// Threads the oracle's OpenMP loops use.
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 }  // extern "C"

@@ -47,6 +47,7 @@ struct Scheme {
 
 // ---------------------------------------------------------------- scalar helpers
 inline double value(double x) { return x; }
+inline double value(long double x) { return (double)x; }
 using std::sqrt;
 using std::fabs;
 

@@ -37,8 +37,14 @@ _L = C.POINTER(C.c_long)
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = C.CDLL(path)
+        _lib = load_library(_build.build())
+    return _lib
+
+
+def load_library(path: str):
+    """Load an oracle shared library and declare its C signatures."""
+    L = C.CDLL(path)
+    if True:
         GP, SP = C.POINTER(Grid), C.POINTER(Scheme)
         L.orc_residual.argtypes = [GP, SP, _D, _D]
         L.orc_time_step.argtypes = [GP, SP, _D]
@@ -47,7 +53,9 @@ def lib():
         L.orc_rk3_step.restype = C.c_double
         L.orc_run.argtypes = [GP, SP, _D, C.c_int, C.c_double, C.c_double]
         L.orc_run.restype = C.c_double
+        L.orc_residual_ext.argtypes = [GP, SP, _D, _D]
         L.orc_residual_cells.argtypes = [GP, SP, _D, C.c_long, _L, _D]
+        L.orc_residual_cells_ext.argtypes = [GP, SP, _D, C.c_long, _L, _D]
         L.orc_roe_flux.argtypes = [SP, C.c_int, C.c_int, _D, _D, _D]
         L.orc_roe_flux.restype = None
         L.orc_physical_flux.argtypes = [SP, C.c_int, C.c_int, _D, _D]
@@ -57,8 +65,9 @@ def lib():
         L.orc_residual_jvp.argtypes = [GP, SP, _D, _D, _D, _D]
         L.orc_rk3_jvp.argtypes = [GP, SP, _D, _D, C.c_int, C.c_double]
         L.orc_count_ops.argtypes = [GP, SP, _D, C.c_double, _L]
-        _lib = L
-    return _lib
+        L.orc_max_threads.argtypes = []
+        L.orc_max_threads.restype = C.c_int
+    return L
 
 
 def grid(g) -> Grid:
@@ -91,13 +100,22 @@ def residual(g, U, s: Scheme | None = None) -> np.ndarray:
     return R
 
 
-def residual_cells(g, U, cells, s: Scheme | None = None) -> np.ndarray:
-    """Residual of the listed cells (flat interior indices); shape (len(cells), nvar)."""
+def residual_ext(g, U, s: Scheme | None = None) -> np.ndarray:
+    """R_h evaluated in extended precision (long double) and rounded to double."""
+    U = _check(g, U)
+    R = np.empty_like(U)
+    lib().orc_residual_ext(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), _ptr(R))
+    return R
+
+
+def residual_cells(g, U, cells, s: Scheme | None = None, extended: bool = False) -> np.ndarray:
+    """Residual of the listed cells (flat interior indices); shape (len(cells), nvar).
+    extended=True evaluates in long double and rounds the result to double."""
     U = _check(g, U)
     cells = np.ascontiguousarray(cells, dtype=np.int64)
     out = np.empty((cells.size, g.nvar), dtype=np.float64)
-    lib().orc_residual_cells(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), cells.size,
-                             cells.ctypes.data_as(_L), _ptr(out))
+    fn = lib().orc_residual_cells_ext if extended else lib().orc_residual_cells
+    fn(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), cells.size, cells.ctypes.data_as(_L), _ptr(out))
     return out
 
 
@@ -159,6 +177,11 @@ def rk3_jvp(g, U, dU, nsteps: int, dt: float, s: Scheme | None = None):
     dU = _check(g, dU).copy()
     lib().orc_rk3_jvp(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), _ptr(dU), nsteps, dt)
     return U, dU
+
+
+def max_threads() -> int:
+    """Threads the oracle's OpenMP loops use on this host."""
+    return lib().orc_max_threads()
 
 
 def count_ops(g, U, dt: float, s: Scheme | None = None) -> dict:

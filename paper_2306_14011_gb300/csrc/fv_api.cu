@@ -1,0 +1,539 @@
+// Host side of the libfv C ABI (declared in include/fv.h): contexts, argument
+// validation, TMA tensor maps, host-pointer staging and the CUDA-graph step
+// driver.  Every numerical step runs in the kernels of fv_stage*.cu and
+// fv_reduce.cu.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/fv.h"
+#include "fv_device.cuh"
+#include "fv_internal.h"
+
+using namespace fvk;
+
+namespace {
+
+#define FV_CK(call)                                 \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_);    \
+  } while (0)
+
+int cuda_fail(cudaError_t e) {
+  (void)cudaGetLastError();  // clear a sticky launch error so the next call can proceed
+  return e == cudaErrorMemoryAllocation ? FV_ENOMEM : FV_ECUDA;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct GraphEntry {
+  const double *U;
+  long long dt_bits;  // fixed dt bits, or 0 for CFL steps
+  int steps;
+  cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct fv_ctx {
+  fv_grid grid;
+  fv_scheme scheme;
+  fv_launch launch;
+  cudaStream_t stream;
+  cudaStream_t cap;  // capture stream for graphs
+  int device, sms;
+  size_t smem_optin;
+  int nv;
+  long long ncells;
+  size_t state_bytes;
+  double *U1, *U2;            // RK stage buffers
+  double *stage_in, *stage_out;  // host-pointer staging (lazy)
+  unsigned long long *smax;   // scratch: bits of the max wave-speed sum
+  unsigned *flags;            // scratch: device flags
+  double *t_acc;              // scratch: simulated time
+  double *dt_dev;             // scratch: dt for device outputs
+  double *norm_out;           // scratch: nvar norms
+  double *norm_part;          // scratch: per-CTA partials (lazy)
+  long long norm_part_cap;
+  std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+int validate_grid(const fv_grid *g) {
+  if (!g || (g->dim != 2 && g->dim != 3)) return FV_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    const bool active = d < g->dim;
+    if (active) {
+      if (g->n[d] < 1 || !(g->len[d] > 0.0)) return FV_EINVAL;
+      for (int s = 0; s < 2; ++s)
+        if (g->bc[d][s] != FV_BC_PERIODIC && g->bc[d][s] != FV_BC_TRANSMISSIVE) return FV_EINVAL;
+      if ((g->bc[d][0] == FV_BC_PERIODIC) != (g->bc[d][1] == FV_BC_PERIODIC)) return FV_EINVAL;
+    } else if (g->n[d] != 1) {
+      return FV_EINVAL;
+    }
+  }
+  const long long cells = (long long)g->n[0] * g->n[1] * g->n[2];
+  if (cells * (g->dim + 2) >= (1ll << 40)) return FV_EINVAL;
+  return FV_OK;
+}
+
+int validate_scheme(const fv_scheme *s) {
+  if (!s || !(s->gamma > 1.0) || !(s->cfl > 0.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0))
+    return FV_EINVAL;
+  return FV_OK;
+}
+
+int validate_launch(const fv_grid *g, const fv_launch *l, size_t smem_optin) {
+  for (int s = 0; s < 3; ++s) {
+    const fv_kernel_cfg &k = l->stage[s];
+    for (int d = 0; d < 3; ++d) {
+      if (d < g->dim) {
+        if (k.tile[d] < 2 || k.tile[d] > 252) return FV_EINVAL;
+      } else if (k.tile[d] != 1) {
+        return FV_EINVAL;
+      }
+    }
+    if (k.tile[0] % 2) return FV_EINVAL;  // TMA boxes start on 16-byte boundaries
+    if (k.threads < 32 || k.threads > 256 || k.threads % 32) return FV_EINVAL;
+    if (k.grid != 0) return FV_EINVAL;  // tiled kernels cover the domain
+    if (k.loader != FV_LOADER_TMA && k.loader != FV_LOADER_PLAIN) return FV_EINVAL;
+    if (stage_smem_bytes(g->dim, k.tile) > smem_optin) return FV_EINVAL;
+  }
+  if (l->dt.threads < 32 || l->dt.threads > 1024 || l->dt.threads % 32 || l->dt.grid < 0) return FV_EINVAL;
+  return FV_OK;
+}
+
+void ntiles(const fv_grid &g, const int tile[3], int nt[3]) {
+  for (int d = 0; d < 3; ++d) nt[d] = (d < g.dim) ? (g.n[d] + tile[d] - 1) / tile[d] : 1;
+}
+
+// TMA tensor map over a state array: dims (x, y[, z], var), box = tile + halo.
+bool make_tmap(const fv_ctx *c, const double *U, const int tile[3], CUtensorMap *map) {
+  const fv_grid &g = c->grid;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  if (g.n[0] % 2) return false;                          // row stride must be a multiple of 16 bytes
+  if (reinterpret_cast<uintptr_t>(U) % 16) return false;  // base address alignment
+  const int box[3] = {tile[0] + 4, tile[1] + 4, tile[2] + 4};
+  for (int d = 0; d < g.dim; ++d)
+    if (box[d] > 256 || box[d] > g.n[d]) return false;
+  cuuint64_t dims[4], strides[3];
+  cuuint32_t boxd[4], estr[4] = {1, 1, 1, 1};
+  const int rank = g.dim + 1;
+  cuuint64_t stride = sizeof(double);
+  for (int d = 0; d < g.dim; ++d) {
+    dims[d] = (cuuint64_t)g.n[d];
+    boxd[d] = (cuuint32_t)box[d];
+    stride *= (cuuint64_t)g.n[d];
+    strides[d] = stride;  // byte stride of dimension d+1
+  }
+  dims[g.dim] = (cuuint64_t)c->nv;
+  boxd[g.dim] = (cuuint32_t)c->nv;
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<double *>(U), dims, strides,
+                   boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, double *out,
+          const unsigned long long *smax, double dt_fixed, double *norm_part, double *t_acc, cudaStream_t st) {
+  const fv_grid &g = c->grid;
+  const fv_kernel_cfg &k = c->launch.stage[sidx];
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  a.Us = Us;
+  a.Un = Un;
+  a.out = out;
+  a.norm_part = norm_part;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = g.n[d];
+    a.tile[d] = k.tile[d];
+    a.bc[d][0] = g.bc[d][0];
+    a.bc[d][1] = g.bc[d][1];
+  }
+  ntiles(g, k.tile, a.ntile);
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (d < g.dim) ? g.len[d] / g.n[d] : 1.0;
+  for (int d = 0; d < 3; ++d) {
+    double ds = 1.0;  // area of a face normal to axis d
+    for (int e = 0; e < g.dim; ++e)
+      if (e != d) ds *= h[e];
+    a.half_ds[d] = 0.5 * ds;  // halved: the flux routine returns 2F
+    a.half_inv_h[d] = 0.5 / h[d];
+  }
+  a.g1 = c->scheme.gamma - 1.0;
+  a.half_eps = 0.5 * c->scheme.eps;
+  a.efix = c->scheme.efix;
+  a.inv2efix = c->scheme.efix > 0.0 ? 0.5 / c->scheme.efix : 0.0;
+  a.smax = smax;
+  a.cfl = c->scheme.cfl;
+  a.dt_fixed = dt_fixed;
+  a.t_acc = t_acc;
+  a.flags = c->flags;
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  a.use_tma = (k.loader == FV_LOADER_TMA && make_tmap(c, Us, k.tile, &map)) ? 1 : 0;
+  FV_CK(launch_stage(g.dim, mode, &map, a, k.threads, st));
+  return FV_OK;
+}
+
+int dt_launch(fv_ctx *c, const double *U, cudaStream_t st) {
+  DtArgs a;
+  memset(&a, 0, sizeof(a));
+  a.U = U;
+  a.ncells = c->ncells;
+  a.dim = c->grid.dim;
+  a.g1 = c->scheme.gamma - 1.0;
+  a.gamma = c->scheme.gamma;
+  for (int d = 0; d < 3; ++d) a.inv_h[d] = (d < c->grid.dim) ? c->grid.n[d] / c->grid.len[d] : 0.0;
+  a.smax = c->smax;
+  a.flags = c->flags;
+  int blocks = c->launch.dt.grid > 0 ? c->launch.dt.grid : 2 * c->sms;
+  const long long need = (c->ncells + c->launch.dt.threads - 1) / c->launch.dt.threads;
+  if (blocks > need) blocks = (int)(need > 0 ? need : 1);
+  FV_CK(cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), st));
+  FV_CK(launch_dt(a, blocks, c->launch.dt.threads, st));
+  return FV_OK;
+}
+
+// One SSP-RK3 step on device state U (stream st).  smax_mode: dt from CFL.
+int rk_step_device(fv_ctx *c, double *U, double dt_fixed, bool cfl, double *t_acc, cudaStream_t st) {
+  int r;
+  const unsigned long long *sm = nullptr;
+  if (cfl) {
+    if ((r = dt_launch(c, U, st))) return r;
+    sm = c->smax;
+  }
+  if ((r = stage(c, MODE_STAGE1, 0, U, U, c->U1, sm, dt_fixed, nullptr, nullptr, st))) return r;
+  if ((r = stage(c, MODE_STAGE2, 1, c->U1, U, c->U2, sm, dt_fixed, nullptr, nullptr, st))) return r;
+  if ((r = stage(c, MODE_STAGE3, 2, c->U2, U, U, sm, dt_fixed, nullptr, t_acc, st))) return r;
+  return FV_OK;
+}
+
+int ensure_staging(fv_ctx *c) {
+  if (!c->stage_in) FV_CK(cudaMalloc(&c->stage_in, c->state_bytes));
+  if (!c->stage_out) FV_CK(cudaMalloc(&c->stage_out, c->state_bytes));
+  return FV_OK;
+}
+
+int read_flags(fv_ctx *c) {
+  unsigned f = 0;
+  FV_CK(cudaMemcpyAsync(&f, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  FV_CK(cudaStreamSynchronize(c->stream));
+  if (f) FV_CK(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream));
+  if (f & FLAG_TIMEOUT) return FV_ETIMEOUT;
+  if (f & FLAG_NONPHYSICAL) return FV_ENONPHYSICAL;
+  return FV_OK;
+}
+
+int set_attributes(fv_ctx *c) {
+  size_t mx = 0;
+  for (int s = 0; s < 3; ++s) {
+    const size_t b = stage_smem_bytes(c->grid.dim, c->launch.stage[s].tile);
+    mx = b > mx ? b : mx;
+  }
+  FV_CK(stage_kernel_attributes(c->grid.dim, mx));
+  return FV_OK;
+}
+
+void drop_graphs(fv_ctx *c) {
+  for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fv_strerror(int status) {
+  switch (status) {
+    case FV_OK: return "success";
+    case FV_EINVAL: return "invalid argument";
+    case FV_ENOMEM: return "out of memory";
+    case FV_ECUDA: return "CUDA error";
+    case FV_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
+    case FV_ETIMEOUT: return "device-side wait timed out";
+    case FV_EUNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+int fv_default_launch(const fv_grid *g, fv_launch *l) {
+  if (!l || validate_grid(g)) return FV_EINVAL;
+  memset(l, 0, sizeof(*l));
+  for (int s = 0; s < 3; ++s) {
+    fv_kernel_cfg &k = l->stage[s];
+    if (g->dim == 2) {
+      k.tile[0] = 32;
+      k.tile[1] = 16;
+      k.tile[2] = 1;
+    } else {
+      k.tile[0] = 16;
+      k.tile[1] = 8;
+      k.tile[2] = 4;
+    }
+    k.threads = 256;
+    k.grid = 0;
+  }
+  l->dt.threads = 256;
+  l->dt.grid = 0;
+  return FV_OK;
+}
+
+int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, const fv_launch *l, void *stream) {
+  if (!out) return FV_EINVAL;
+  *out = nullptr;
+  if (ngrids < 1) return FV_EINVAL;
+  if (validate_grid(grids) || validate_scheme(s)) return FV_EINVAL;
+  if (ngrids > 1) return FV_EUNSUPPORTED;
+  fv_ctx *c = new (std::nothrow) fv_ctx();
+  if (!c) return FV_ENOMEM;
+  c->grid = grids[0];
+  c->scheme = *s;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->nv = grids[0].dim + 2;
+  c->ncells = (long long)grids[0].n[0] * grids[0].n[1] * grids[0].n[2];
+  c->state_bytes = sizeof(double) * (size_t)c->nv * (size_t)c->ncells;
+  int r = FV_OK;
+  auto fail = [&](int code) {
+    fv_destroy(c);
+    return code;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(cuda_fail(cudaErrorNoDevice));
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return fail(FV_ECUDA);
+  c->sms = prop.multiProcessorCount;
+  c->smem_optin = prop.sharedMemPerBlockOptin;
+  if (l)
+    c->launch = *l;
+  else
+    fv_default_launch(&c->grid, &c->launch);
+  if ((r = validate_launch(&c->grid, &c->launch, c->smem_optin))) return fail(r);
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(FV_ECUDA);
+  if (cudaMalloc(&c->U1, c->state_bytes) != cudaSuccess || cudaMalloc(&c->U2, c->state_bytes) != cudaSuccess)
+    return fail(cuda_fail(cudaErrorMemoryAllocation));
+  // scratch: smax (8) | flags (8) | t_acc (8) | dt (8) | norms (8 * 5)
+  char *scr = nullptr;
+  if (cudaMalloc(&scr, 256) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
+  c->smax = reinterpret_cast<unsigned long long *>(scr);
+  c->flags = reinterpret_cast<unsigned *>(scr + 8);
+  c->t_acc = reinterpret_cast<double *>(scr + 16);
+  c->dt_dev = reinterpret_cast<double *>(scr + 24);
+  c->norm_out = reinterpret_cast<double *>(scr + 32);
+  if (cudaMemset(scr, 0, 256) != cudaSuccess) return fail(FV_ECUDA);
+  if ((r = set_attributes(c))) return fail(r);
+  *out = c;
+  return FV_OK;
+}
+
+int fv_set_launch(fv_ctx *c, const fv_launch *l) {
+  if (!c || !l) return FV_EINVAL;
+  int r = validate_launch(&c->grid, l, c->smem_optin);
+  if (r) return r;
+  c->launch = *l;
+  drop_graphs(c);
+  return set_attributes(c);
+}
+
+int fv_get_launch(const fv_ctx *c, fv_launch *l) {
+  if (!c || !l) return FV_EINVAL;
+  *l = c->launch;
+  return FV_OK;
+}
+
+int fv_residual(fv_ctx *c, const double *U, double *R, double *rnorm2) {
+  if (!c || !U || !R || U == R) return FV_EINVAL;
+  int r;
+  const bool hostU = !is_device_ptr(U), hostR = !is_device_ptr(R);
+  const bool hostN = rnorm2 && !is_device_ptr(rnorm2);
+  if ((hostU || hostR) && (r = ensure_staging(c))) return r;
+  const double *Ud = U;
+  double *Rd = R;
+  if (hostU) {
+    FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyHostToDevice, c->stream));
+    Ud = c->stage_in;
+  }
+  if (hostR) Rd = c->stage_out;
+  double *part = nullptr;
+  int nt[3];
+  ntiles(c->grid, c->launch.stage[0].tile, nt);
+  const long long nblk = (long long)nt[0] * nt[1] * nt[2];
+  if (rnorm2) {
+    if (c->norm_part_cap < nblk) {
+      if (c->norm_part) cudaFree(c->norm_part);
+      c->norm_part = nullptr;
+      c->norm_part_cap = 0;
+      FV_CK(cudaMalloc(&c->norm_part, sizeof(double) * c->nv * nblk));
+      c->norm_part_cap = nblk;
+    }
+    part = c->norm_part;
+  }
+  if ((r = stage(c, MODE_RESIDUAL, 0, Ud, Ud, Rd, nullptr, 0.0, part, nullptr, c->stream))) return r;
+  if (rnorm2) {
+    FV_CK(launch_norm_finalize(part, (int)nblk, c->nv, c->norm_out, c->stream));
+    FV_CK(cudaMemcpyAsync(rnorm2, c->norm_out, sizeof(double) * c->nv,
+                          hostN ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream));
+  }
+  if (hostR) FV_CK(cudaMemcpyAsync(R, Rd, c->state_bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (hostU || hostR || hostN) FV_CK(cudaStreamSynchronize(c->stream));
+  return FV_OK;
+}
+
+int fv_time_step(fv_ctx *c, const double *U, double *dt_out) {
+  if (!c || !U || !dt_out) return FV_EINVAL;
+  int r;
+  const bool hostU = !is_device_ptr(U), hostD = !is_device_ptr(dt_out);
+  const double *Ud = U;
+  if (hostU) {
+    if ((r = ensure_staging(c))) return r;
+    FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyHostToDevice, c->stream));
+    Ud = c->stage_in;
+  }
+  if ((r = dt_launch(c, Ud, c->stream))) return r;
+  if (!hostD) {
+    FV_CK(launch_dt_finalize(c->smax, c->scheme.cfl, dt_out, c->stream));
+    return hostU ? read_flags(c) : FV_OK;
+  }
+  unsigned long long bits = 0;
+  FV_CK(cudaMemcpyAsync(&bits, c->smax, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+  if ((r = read_flags(c))) return r;
+  double smax;
+  memcpy(&smax, &bits, sizeof(smax));
+  *dt_out = c->scheme.cfl / smax;
+  return FV_OK;
+}
+
+int fv_rk_step(fv_ctx *c, double *U, double dt, double *dt_used) {
+  if (!c || !U) return FV_EINVAL;
+  int r;
+  const bool hostU = !is_device_ptr(U);
+  double *Ud = U;
+  if (hostU) {
+    if ((r = ensure_staging(c))) return r;
+    FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyHostToDevice, c->stream));
+    Ud = c->stage_in;
+  }
+  const bool cfl = !(dt > 0.0);
+  if (dt_used) FV_CK(cudaMemsetAsync(c->t_acc, 0, sizeof(double), c->stream));
+  if ((r = rk_step_device(c, Ud, cfl ? 0.0 : dt, cfl, dt_used ? c->t_acc : nullptr, c->stream))) return r;
+  if (hostU) FV_CK(cudaMemcpyAsync(U, Ud, c->state_bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (dt_used) {
+    FV_CK(cudaMemcpyAsync(dt_used, c->t_acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return read_flags(c);
+  }
+  if (hostU) FV_CK(cudaStreamSynchronize(c->stream));
+  return FV_OK;
+}
+
+int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
+  if (!c || !U || nsteps < 0) return FV_EINVAL;
+  int r;
+  const bool hostU = !is_device_ptr(U);
+  double *Ud = U;
+  if (hostU) {
+    if ((r = ensure_staging(c))) return r;
+    FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyHostToDevice, c->stream));
+    Ud = c->stage_in;
+  }
+  const bool cfl = !(dt_fixed > 0.0);
+  long long dbits = 0;
+  if (!cfl) memcpy(&dbits, &dt_fixed, sizeof(dbits));
+  FV_CK(cudaMemsetAsync(c->t_acc, 0, sizeof(double), c->stream));
+  // Graphs of K steps and of one step, both captured on the first call for
+  // this (U, dt mode) so that later calls only replay.
+  const int K = 16;
+  cudaGraphExec_t gK = nullptr, g1 = nullptr;
+  for (auto &g : c->graphs)
+    if (g.U == Ud && g.dt_bits == dbits) (g.steps == K ? gK : g1) = g.exec;
+  for (int pass = 0; pass < 2 && nsteps > 0; ++pass) {
+    const int steps = pass == 0 ? K : 1;
+    if ((pass == 0 ? gK : g1) != nullptr) continue;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec = nullptr;
+    r = FV_OK;
+    FV_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    for (int s = 0; s < steps && r == FV_OK; ++s) r = rk_step_device(c, Ud, dt_fixed, cfl, c->t_acc, c->cap);
+    cudaError_t ec = cudaStreamEndCapture(c->cap, &graph);
+    if (r) {
+      if (ec == cudaSuccess) cudaGraphDestroy(graph);
+      return r;
+    }
+    FV_CK(ec);
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    FV_CK(ei);
+    c->graphs.push_back(GraphEntry{Ud, dbits, steps, exec});
+    (pass == 0 ? gK : g1) = exec;
+  }
+  for (int left = nsteps; left > 0;) {
+    const int steps = left >= K ? K : 1;
+    FV_CK(cudaGraphLaunch(steps == K ? gK : g1, c->stream));
+    left -= steps;
+  }
+  if (hostU) FV_CK(cudaMemcpyAsync(U, Ud, c->state_bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (t_out) {
+    FV_CK(cudaMemcpyAsync(t_out, c->t_acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return read_flags(c);
+  }
+  if (hostU) FV_CK(cudaStreamSynchronize(c->stream));
+  return FV_OK;
+}
+
+int fv_sync(fv_ctx *c) {
+  if (!c) return FV_EINVAL;
+  return read_flags(c);
+}
+
+void fv_destroy(fv_ctx *c) {
+  if (!c) return;
+  if (c->stream || c->U1) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->U1) cudaFree(c->U1);
+  if (c->U2) cudaFree(c->U2);
+  if (c->stage_in) cudaFree(c->stage_in);
+  if (c->stage_out) cudaFree(c->stage_out);
+  if (c->smax) cudaFree(c->smax);  // start of the scratch block
+  if (c->norm_part) cudaFree(c->norm_part);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, void *stream) {
+  if (!x || !out_rsqrt || !out_rcp || n < 0) return FV_EINVAL;
+  FV_CK(launch_debug_math(x, out_rsqrt, out_rcp, n, static_cast<cudaStream_t>(stream)));
+  return FV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,248 @@
+// Device-side building blocks of the FP64 Euler kernels (sm_103a).
+//
+// Design note.  On GB300 the FP64 pipe retires about two lane-operations per
+// clock per SM (~0.6 T FP64 instructions/s per GPU), roughly sixty times less
+// than what HBM can feed to this stencil; the FP64 pipe, not memory, bounds
+// every kernel here.  So:
+//   * comparisons, absolute values, min/max and the minmod limiter run on the
+//     integer pipe, on IEEE-754 bit patterns (exact for finite doubles);
+//   * reciprocals and reciprocal square roots start from the PTX
+//     rcp.approx.ftz.f64 / rsqrt.approx.ftz.f64 seeds (issued on the
+//     special-function unit, relative error below 2^-20) and are refined to
+//     full double precision by one third-order Householder step in FMA;
+//   * the Roe flux is arranged so each quantity is formed once and the 1/2 of
+//     the flux is folded into the caller's scale (roe_2F returns 2F).
+#pragma once
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace fvk {
+
+// ------------------------------------------------------------ device flags
+enum : unsigned { FLAG_NONPHYSICAL = 1u, FLAG_TIMEOUT = 2u };
+
+// ------------------------------------------------------------ integer-pipe helpers
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// |x| by clearing the sign bit.
+__device__ __forceinline__ double iabs(double x) {
+  return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
+}
+
+// a < b for non-negative finite doubles (bit patterns are ordered like the values).
+__device__ __forceinline__ bool ilt_nonneg(double a, double b) { return dbits(a) < dbits(b); }
+
+// minmod(a, b): 0 when the signs differ (or either is zero), else the argument
+// of smaller magnitude.  Bitwise equal to the branchy definition for finite
+// inputs (a zero argument yields a signed zero, which adds as zero).
+__device__ __forceinline__ double minmod(double a, double b) {
+  const long long ia = dbits(a), ib = dbits(b);
+  const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
+  const double m = (ma < mb) ? a : b;
+  return ((ia ^ ib) < 0) ? 0.0 : m;
+}
+
+// true when x is not a finite positive double (x <= 0, -0, inf or NaN).
+__device__ __forceinline__ bool not_positive_finite(double x) {
+  const long long ix = dbits(x);
+  return ix <= 0 || ix >= 0x7ff0000000000000ll;
+}
+
+// ------------------------------------------------------------ reciprocal and rsqrt
+__device__ __forceinline__ double rsqrt_seed(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+__device__ __forceinline__ double rcp_seed(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+
+// 1/sqrt(x) for positive normal x.  With y0 the seed and e = 1 - x*y0^2,
+// 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)); truncating
+// the binomial series after e^2 is the third-order Householder step, so
+// |e| < 2^-20 leaves a truncation error below 2^-59 (5 FP64 operations).
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+  const double y = rsqrt_seed(x);
+  const double t = x * y;
+  const double e = fma(-t, y, 1.0);
+  const double c = fma(e, 0.375, 0.5);
+  const double ye = y * e;
+  return fma(ye, c, y);
+}
+
+// 1/x for normal x: 1/x = y0 / (1 - e) with e = 1 - x*y0, so
+// 1/x = y0 (1 + e + e^2 + O(e^3)) (3 FP64 operations, same truncation order).
+__device__ __forceinline__ double rcp_fp64(double x) {
+  const double y = rcp_seed(x);
+  const double e = fma(-x, y, 1.0);
+  const double ee = fma(e, e, e);
+  return fma(y, ee, y);
+}
+
+// ------------------------------------------------------------ Roe flux
+// Twice the Roe flux across a face with unit normal along one axis.  States
+// are ordered normal-first: q = (rho, m_n, m_t[0..NT-1], rho*e_t), where m_n
+// is the momentum along the face normal and m_t the tangential momenta.
+//   2F = F(QL) + F(QR) - sum_w |lambda_w| alpha_w r_w
+// acoustic waves alpha_{1,3} = (dp -+ rho~ c~ du_n) / (2 c~^2), entropy wave
+// alpha_2 = drho - dp / c~^2, shear waves rho~ du_t, eigenvalues u~_n -+ c~
+// and u~_n; Harten's fix replaces |lambda| by (lambda^2 + delta^2)/(2 delta)
+// for the acoustic waves when |lambda| < delta = efix * c~.
+// g1 = gamma - 1; inv2efix = 1 / (2 efix) (unused when efix = 0).
+template <int NT>
+__device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
+                                       double efix, double inv2efix, double (&G)[NT + 3]) {
+  constexpr int E = NT + 2;
+  // left primitives: 1/sqrt(rho) gives both sqrt(rho) and 1/rho
+  const double tL = rsqrt_fp64(QL[0]);
+  const double rL = tL * tL;
+  const double sL = QL[0] * tL;
+  const double unL = QL[1] * rL;
+  double utL[NT];
+  double kL = QL[1] * unL;  // rho |u|^2
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    utL[t] = QL[2 + t] * rL;
+    kL = fma(QL[2 + t], utL[t], kL);
+  }
+  const double pL = g1 * fma(-0.5, kL, QL[E]);
+  const double eL = QL[E] + pL;  // rho h_t
+  const double HL = eL * rL;
+  // right primitives
+  const double tR = rsqrt_fp64(QR[0]);
+  const double rR = tR * tR;
+  const double sR = QR[0] * tR;
+  const double unR = QR[1] * rR;
+  double utR[NT];
+  double kR = QR[1] * unR;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    utR[t] = QR[2 + t] * rR;
+    kR = fma(QR[2 + t], utR[t], kR);
+  }
+  const double pR = g1 * fma(-0.5, kR, QR[E]);
+  const double eR = QR[E] + pR;
+  const double HR = eR * rR;
+
+  // Roe averages with sqrt(rho) weights
+  const double inv = rcp_fp64(sL + sR);
+  const double wL = sL * inv, wR = sR * inv;
+  const double un = fma(wL, unL, wR * unR);
+  double ut[NT];
+  double q2 = un * un;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    ut[t] = fma(wL, utL[t], wR * utR[t]);
+    q2 = fma(ut[t], ut[t], q2);
+  }
+  const double H = fma(wL, HL, wR * HR);
+  const double rho = sL * sR;
+  const double hq = 0.5 * q2;
+  const double c2 = g1 * (H - hq);
+  const double tc = rsqrt_fp64(c2);  // 1/c~
+  const double c = c2 * tc;
+  const double ic2 = tc * tc;        // 1/c~^2
+
+  // wave strengths
+  const double drho = QR[0] - QL[0];
+  const double dp = pR - pL;
+  const double dun = unR - unL;
+  const double rcdun = (rho * c) * dun;
+  const double hic2 = 0.5 * ic2;
+  const double a1 = (dp - rcdun) * hic2;
+  const double a3 = (dp + rcdun) * hic2;
+  const double a2 = fma(-dp, ic2, drho);
+
+  // |eigenvalues| (sign handling on the integer pipe), entropy fix
+  double l1 = iabs(un - c);
+  double l3 = iabs(un + c);
+  const double l2 = iabs(un);
+  const double delta = efix * c;
+  if (ilt_nonneg(l1, delta)) l1 = fma(l1, l1, delta * delta) * (tc * inv2efix);
+  if (ilt_nonneg(l3, delta)) l3 = fma(l3, l3, delta * delta) * (tc * inv2efix);
+
+  // dissipation sum_w |lambda_w| alpha_w r_w
+  const double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3;
+  const double lr = l2 * rho;
+  const double s13 = A1 + A3;
+  const double cd13 = c * (A3 - A1);
+  const double D0 = s13 + A2;
+  const double Dn = fma(un, D0, cd13);
+  double DE = hq * A2;
+  double Dt[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const double B = lr * (utR[t] - utL[t]);
+    Dt[t] = fma(ut[t], D0, B);
+    DE = fma(ut[t], B, DE);
+  }
+  DE = fma(H, s13, fma(un, cd13, DE));
+
+  // F(QL) + F(QR) - dissipation
+  G[0] = (QL[1] + QR[1]) - D0;
+  G[1] = (fma(QL[1], unL, pL) + fma(QR[1], unR, pR)) - Dn;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) G[2 + t] = fma(QL[1], utL[t], QR[1] * utR[t]) - Dt[t];
+  G[E] = fma(unL, eL, unR * eR) - DE;
+}
+
+// ------------------------------------------------------------ mbarrier / TMA (inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the barrier, giving up after limit_ns of wall
+// time (checked every 256 polls).  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u && globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// TMA tiled loads into shared memory, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+}  // namespace fvk

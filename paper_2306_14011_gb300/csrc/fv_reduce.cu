@@ -1,0 +1,142 @@
+// Grid reductions of libfv: the CFL time step and the residual norms, plus
+// the device-arithmetic diagnostic.
+#include "fv_device.cuh"
+#include "fv_internal.h"
+#include "fv_stage.cuh"
+
+namespace fvk {
+
+size_t stage_smem_bytes(int dim, const int tile[3]) {
+  const TileGeom G = tile_geom(dim, tile);
+  const int nv = dim + 2;
+  return 128 + sizeof(double) * (size_t)nv * (G.plane + G.fmax + G.cells) + 16;
+}
+
+cudaError_t launch_stage_2d(int, const CUtensorMap *, const StageArgs &, int, cudaStream_t);
+cudaError_t launch_stage_3d(int, const CUtensorMap *, const StageArgs &, int, cudaStream_t);
+cudaError_t set_stage_attributes_2d(size_t);
+cudaError_t set_stage_attributes_3d(size_t);
+
+cudaError_t launch_stage(int dim, int mode, const CUtensorMap *tmap, const StageArgs &a, int threads,
+                         cudaStream_t st) {
+  return dim == 2 ? launch_stage_2d(mode, tmap, a, threads, st) : launch_stage_3d(mode, tmap, a, threads, st);
+}
+
+cudaError_t stage_kernel_attributes(int dim, size_t smem) {
+  return dim == 2 ? set_stage_attributes_2d(smem) : set_stage_attributes_3d(smem);
+}
+
+// Maximum over cells of sum_d (|u_d| + c) / dx_d, c = sqrt(gamma p / rho),
+// reduced exactly (max of non-negative doubles = max of their bit patterns):
+// per thread, warp shuffle, CTA, then one atomicMax per CTA.  Cells with
+// rho <= 0, p <= 0 or NaN raise FLAG_NONPHYSICAL and are left out.
+template <int DIM>
+__global__ void __launch_bounds__(1024) dt_kernel(const DtArgs a) {
+  constexpr int NV = DIM + 2;
+  const long long N = a.ncells;
+  unsigned long long best = 0ull;
+  bool bad = false;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+    const double rho = a.U[c];
+    if (not_positive_finite(rho)) {
+      bad = true;
+      continue;
+    }
+    const double tr = rsqrt_fp64(rho);
+    const double r = tr * tr;
+    double u[DIM];
+    double k = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const double m = a.U[(1 + d) * N + c];
+      u[d] = m * r;
+      k = (d == 0) ? m * u[d] : fma(m, u[d], k);
+    }
+    const double p = a.g1 * fma(-0.5, k, a.U[(NV - 1) * N + c]);
+    if (not_positive_finite(p)) {
+      bad = true;
+      continue;
+    }
+    const double c2 = (a.gamma * p) * r;
+    const double cs = c2 * rsqrt_fp64(c2);
+    double s = (iabs(u[0]) + cs) * a.inv_h[0];
+#pragma unroll
+    for (int d = 1; d < DIM; ++d) s = fma(iabs(u[d]) + cs, a.inv_h[d], s);
+    const unsigned long long sb = (unsigned long long)dbits(s);
+    best = sb > best ? sb : best;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+    best = o > best ? o : best;
+  }
+  __shared__ unsigned long long wmax[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wmax[warp] = best;
+  const int anybad = __syncthreads_or(bad);
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    unsigned long long m = lane < nw ? wmax[lane] : 0ull;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+      m = o > m ? o : m;
+    }
+    if (lane == 0) {
+      atomicMax(a.smax, m);
+      if (anybad) atomicOr(a.flags, FLAG_NONPHYSICAL);
+    }
+  }
+}
+
+cudaError_t launch_dt(const DtArgs &a, int blocks, int threads, cudaStream_t st) {
+  if (a.dim == 2)
+    dt_kernel<2><<<blocks, threads, 0, st>>>(a);
+  else
+    dt_kernel<3><<<blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Sum of per-CTA partials, one warp per variable, in a fixed order (strided
+// lane sums, then a fixed shuffle tree), so the result is run-to-run exact.
+__global__ void norm_finalize_kernel(const double *part, int nparts, int nvar, double *out) {
+  const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (v >= nvar) return;
+  double s = 0.0;
+  for (int q = lane; q < nparts; q += 32) s += part[(long long)q * nvar + v];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) out[v] = s;
+}
+
+cudaError_t launch_norm_finalize(const double *part, int nparts, int nvar, double *out, cudaStream_t st) {
+  norm_finalize_kernel<<<1, 32 * nvar, 0, st>>>(part, nparts, nvar, out);
+  return cudaGetLastError();
+}
+
+// dt = cfl / smax on the device (for a device-pointer dt_out).
+__global__ void dt_finalize_kernel(const unsigned long long *smax, double cfl, double *out) {
+  *out = cfl / __longlong_as_double((long long)*smax);
+}
+
+cudaError_t launch_dt_finalize(const unsigned long long *smax, double cfl, double *out, cudaStream_t st) {
+  dt_finalize_kernel<<<1, 1, 0, st>>>(smax, cfl, out);
+  return cudaGetLastError();
+}
+
+__global__ void debug_math_kernel(const double *x, double *o1, double *o2, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    o1[i] = rsqrt_fp64(x[i]);
+    o2[i] = rcp_fp64(x[i]);
+  }
+}
+
+cudaError_t launch_debug_math(const double *x, double *o1, double *o2, long n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  debug_math_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, o1, o2, n);
+  return cudaGetLastError();
+}
+
+}  // namespace fvk

@@ -1,0 +1,326 @@
+// Fused residual / SSP-RK3 stage kernel for 2D and 3D uniform Cartesian grids.
+//
+// One CTA owns a tile of cells.  It
+//   1. stages the tile plus a 2-cell halo of every conserved variable into
+//      shared memory: one TMA box (x, y[, z], var) completing on an mbarrier,
+//      then plain loads for the halo cells that lie outside the domain
+//      (periodic wrap or transmissive copy) -- TMA fills those with zeros;
+//      without a tensor map (odd nx, tiny grids) every cell is a plain load;
+//   2. per axis d, computes every face flux of the tile exactly once: MUSCL
+//      face states of Eq. (6) (eps/2 * minmod slope) and the Roe flux, into a
+//      shared-memory face buffer; faces are spread over all threads so warps
+//      stay full;
+//   3. accumulates R_v = sum_d coef_d (F_{k+1/2} - F_{k-1/2}) per cell in
+//      shared memory, the flux-difference form of Eq. (5);
+//   4. writes the residual, or the SSP-RK3 stage combination of Eq. (4)
+//      discretised in time, for its cells (coalesced along x).
+// Faces on a tile boundary are computed by both neighbouring CTAs (a
+// 1/tile_x + 1/tile_y [+ 1/tile_z] overhead); inside a tile each face is
+// evaluated once.
+#pragma once
+#include "fv_device.cuh"
+#include "fv_internal.h"
+
+namespace fvk {
+
+constexpr uint64_t kTmaWaitNs = 2000000000ull;  // 2 s bound on the tile-load wait
+
+struct TileGeom {
+  int BX, BY, BZ;   // tile box with halo
+  int plane;        // doubles per variable in the box
+  int fmax;         // face-buffer length per variable
+  int cells;        // cells per full tile
+};
+
+__host__ __device__ inline TileGeom tile_geom(int dim, const int tile[3]) {
+  TileGeom g;
+  const int tx = tile[0], ty = tile[1], tz = (dim == 3) ? tile[2] : 1;
+  g.BX = tx + 4;
+  g.BY = ty + 4;
+  g.BZ = (dim == 3) ? tz + 4 : 1;
+  g.plane = g.BX * g.BY * g.BZ;
+  const int fx = (tx + 1) * ty * tz, fy = tx * (ty + 1) * tz, fz = (dim == 3) ? tx * ty * (tz + 1) : 0;
+  g.fmax = fx > fy ? fx : fy;
+  g.fmax = g.fmax > fz ? g.fmax : fz;
+  g.cells = tx * ty * tz;
+  return g;
+}
+
+// Interior index that ghost coordinate c of an axis with n cells reads.
+__device__ __forceinline__ int ghost_source(int c, int n, int bclo, int bchi) {
+  if (c < 0) return bclo == 0 ? ((c % n) + n) % n : 0;
+  if (c >= n) return bchi == 0 ? c % n : n - 1;
+  return c;
+}
+
+// Load halo cells of the tile box (the 4 layers along each axis next to the
+// valid tile, over the valid extent of the other axes).  only_outside: skip
+// cells inside the domain (already staged by TMA).
+template <int DIM>
+__device__ __forceinline__ void load_halo(double *tile, const StageArgs &a, const int o[3], const int ext[3],
+                                          const TileGeom &G, bool only_outside) {
+  constexpr int NV = DIM + 2;
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    if (only_outside && o[d] >= 2 && o[d] + ext[d] + 2 <= a.n[d]) continue;
+    const int a1 = (d == 0) ? 1 : 0, a2 = (d == 2) ? 1 : 2;  // the other two axes
+    const int e1 = ext[a1], e2 = (DIM == 3) ? ext[a2] : 1;
+    const int cnt = 4 * e1 * e2;
+    for (int h = threadIdx.x; h < cnt; h += blockDim.x) {
+      const int layer = h & 3;
+      const int r = h >> 2;
+      int l[3];
+      l[d] = (layer < 2) ? layer : ext[d] + layer;
+      l[a1] = r % e1 + 2;
+      l[a2] = (DIM == 3) ? r / e1 + 2 : 0;
+      int gc[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) gc[q] = o[q] - 2 + l[q];
+      if (DIM == 2) gc[2] = 0;
+      const bool outside = gc[d] < 0 || gc[d] >= a.n[d];
+      if (only_outside && !outside) continue;
+      gc[d] = ghost_source(gc[d], a.n[d], a.bc[d][0], a.bc[d][1]);
+      const long long src = ((long long)gc[2] * a.n[1] + gc[1]) * a.n[0] + gc[0];
+      const int dst = (l[2] * G.BY + l[1]) * G.BX + l[0];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) tile[v * G.plane + dst] = a.Us[v * N + src];
+    }
+  }
+}
+
+// All face fluxes of the tile along axis D into F, then their differences
+// into the cell accumulator R (R = coef * dF for the first axis, += after).
+template <int DIM, int D>
+__device__ __forceinline__ void face_pass(const double *__restrict__ tile, double *__restrict__ F,
+                                          double *__restrict__ R, const StageArgs &a, const int ext[3],
+                                          const TileGeom &G, double coef) {
+  constexpr int NV = DIM + 2;
+  constexpr int NT = DIM - 1;
+  constexpr int E = NV - 1;
+  const int fe0 = ext[0] + (D == 0), fe1 = ext[1] + (D == 1), fe2 = (DIM == 3) ? ext[2] + (D == 2) : 1;
+  const int nf = fe0 * fe1 * fe2;
+  const int sstride = (D == 0) ? 1 : ((D == 1) ? G.BX : G.BX * G.BY);
+  const double h = a.half_eps;
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    const int i = f % fe0;
+    const int rr = f / fe0;
+    const int j = rr % fe1;
+    const int k = rr / fe1;
+    const int lx = (D == 0) ? i : i + 2;
+    const int ly = (D == 1) ? j : j + 2;
+    const int lz = (DIM == 3) ? ((D == 2) ? k : k + 2) : 0;
+    const double *p = tile + (lz * G.BY + ly) * G.BX + lx;
+    double QL[NV], QR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double *pv = p + v * G.plane;
+      const double q0 = pv[0], q1 = pv[sstride], q2 = pv[2 * sstride], q3 = pv[3 * sstride];
+      const double dm = q1 - q0, d0 = q2 - q1, dp = q3 - q2;
+      QL[v] = fma(h, minmod(dm, d0), q1);
+      QR[v] = fma(-h, minmod(d0, dp), q2);
+    }
+    // normal-first ordering: (rho, m_D, tangential momenta, E)
+    double qL[NT + 3], qR[NT + 3], Gf[NT + 3];
+    qL[0] = QL[0];
+    qR[0] = QR[0];
+    qL[1] = QL[1 + D];
+    qR[1] = QR[1 + D];
+    int t = 0;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      if (ax == D) continue;
+      qL[2 + t] = QL[1 + ax];
+      qR[2 + t] = QR[1 + ax];
+      ++t;
+    }
+    qL[E] = QL[E];
+    qR[E] = QR[E];
+    roe_2F<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gf);
+    F[f] = Gf[0];
+    F[(1 + D) * G.fmax + f] = Gf[1];
+    t = 0;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      if (ax == D) continue;
+      F[(1 + ax) * G.fmax + f] = Gf[2 + t];
+      ++t;
+    }
+    F[E * G.fmax + f] = Gf[E];
+  }
+  __syncthreads();
+  const int ncell = ext[0] * ext[1] * ((DIM == 3) ? ext[2] : 1);
+  const int fstride = (D == 0) ? 1 : ((D == 1) ? fe0 : fe0 * fe1);
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = c % ext[0];
+    const int rr = c / ext[0];
+    const int j = rr % ext[1];
+    const int k = rr / ext[1];
+    const int flo = (k * fe1 + j) * fe0 + i;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double dF = F[v * G.fmax + flo + fstride] - F[v * G.fmax + flo];
+      if (D == 0)
+        R[v * G.cells + c] = coef * dF;
+      else
+        R[v * G.cells + c] = fma(coef, dF, R[v * G.cells + c]);
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIM, int MODE>
+__global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
+  constexpr int NV = DIM + 2;
+  extern __shared__ unsigned char smem_raw[];
+  double *tile = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const TileGeom G = tile_geom(DIM, a.tile);
+  double *F = tile + NV * G.plane;
+  double *R = F + NV * G.fmax;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(R + NV * G.cells);
+
+  int b = blockIdx.x;
+  const int bx = b % a.ntile[0];
+  b /= a.ntile[0];
+  const int by = b % a.ntile[1];
+  const int bz = b / a.ntile[1];
+  const int o[3] = {bx * a.tile[0], by * a.tile[1], (DIM == 3) ? bz * a.tile[2] : 0};
+  int ext[3];
+  ext[0] = min(a.tile[0], a.n[0] - o[0]);
+  ext[1] = min(a.tile[1], a.n[1] - o[1]);
+  ext[2] = (DIM == 3) ? min(a.tile[2], a.n[2] - o[2]) : 1;
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+
+  // ---- 1. stage the tile and its halo
+  if (a.use_tma) {
+    const uint32_t bar = smem_u32(mbar);
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(bar, (uint32_t)(NV * G.plane * sizeof(double)));
+      if (DIM == 2)
+        tma_load_3d(smem_u32(tile), &tmap, o[0] - 2, o[1] - 2, 0, bar);
+      else
+        tma_load_4d(smem_u32(tile), &tmap, o[0] - 2, o[1] - 2, o[2] - 2, 0, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0, kTmaWaitNs);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(a.flags, FLAG_TIMEOUT);
+        mbar_wait_bounded(bar, 0, kTmaWaitNs);  // let a late copy land before the CTA exits
+      }
+      return;
+    }
+    load_halo<DIM>(tile, a, o, ext, G, true);
+  } else {
+    const int ncell = ext[0] * ext[1] * ext[2];
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+      const int i = c % ext[0];
+      const int rr = c / ext[0];
+      const int j = rr % ext[1];
+      const int k = rr / ext[1];
+      const long long src = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
+      const int dst = (((DIM == 3) ? k + 2 : 0) * G.BY + (j + 2)) * G.BX + (i + 2);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) tile[v * G.plane + dst] = a.Us[v * N + src];
+    }
+    load_halo<DIM>(tile, a, o, ext, G, false);
+  }
+  __syncthreads();
+
+  // ---- 2./3. face fluxes and their differences per axis
+  double dt = 0.0, w = 0.0;
+  if (MODE != MODE_RESIDUAL) {
+    dt = a.smax ? a.cfl / __longlong_as_double((long long)*a.smax) : a.dt_fixed;
+    w = (MODE == MODE_STAGE1) ? 1.0 : ((MODE == MODE_STAGE2) ? 0.25 : 2.0 / 3.0);
+  }
+  const double cx = (MODE == MODE_RESIDUAL) ? a.half_ds[0] : -w * dt * a.half_inv_h[0];
+  const double cy = (MODE == MODE_RESIDUAL) ? a.half_ds[1] : -w * dt * a.half_inv_h[1];
+  face_pass<DIM, 0>(tile, F, R, a, ext, G, cx);
+  face_pass<DIM, 1>(tile, F, R, a, ext, G, cy);
+  if constexpr (DIM == 3) {
+    const double cz = (MODE == MODE_RESIDUAL) ? a.half_ds[2] : -w * dt * a.half_inv_h[2];
+    face_pass<DIM, 2>(tile, F, R, a, ext, G, cz);
+  }
+
+  // ---- 4. epilogue
+  const int ncell = ext[0] * ext[1] * ext[2];
+  const bool want_norm = (MODE == MODE_RESIDUAL) && a.norm_part != nullptr;
+  double nrm[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) nrm[v] = 0.0;
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = c % ext[0];
+    const int rr = c / ext[0];
+    const int j = rr % ext[1];
+    const int k = rr / ext[1];
+    const long long gi = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
+    const int lc = (((DIM == 3) ? k + 2 : 0) * G.BY + (j + 2)) * G.BX + (i + 2);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double r = R[v * G.cells + c];
+      double outv;
+      if (MODE == MODE_RESIDUAL) {
+        outv = r;
+        if (want_norm) nrm[v] = fma(r, r, nrm[v]);
+      } else if (MODE == MODE_STAGE1) {
+        outv = tile[v * G.plane + lc] + r;
+      } else if (MODE == MODE_STAGE2) {
+        outv = fma(0.75, a.Un[v * N + gi], 0.25 * tile[v * G.plane + lc]) + r;
+      } else {
+        outv = fma(1.0 / 3.0, a.Un[v * N + gi], (2.0 / 3.0) * tile[v * G.plane + lc]) + r;
+      }
+      a.out[v * N + gi] = outv;
+    }
+  }
+  if (MODE == MODE_STAGE3 && a.t_acc && blockIdx.x == 0 && threadIdx.x == 0) *a.t_acc += dt;
+
+  if (want_norm) {
+    // CTA partial sums of R_v^2 (fixed reduction order: lanes, then warps)
+    __shared__ double red[NV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = nrm[v];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+      if (lane == 0) red[v][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+      double s = 0.0;
+      const int nw = (blockDim.x + 31) >> 5;
+      for (int q = 0; q < nw; ++q) s += red[threadIdx.x][q];
+      a.norm_part[(long long)blockIdx.x * NV + threadIdx.x] = s;
+    }
+  }
+}
+
+template <int DIM>
+cudaError_t launch_stage_dim(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st) {
+  const size_t smem = stage_smem_bytes(DIM, a.tile);
+  const long long nblk = (long long)a.ntile[0] * a.ntile[1] * a.ntile[2];
+  const dim3 grid((unsigned)nblk), block(threads);
+  switch (mode) {
+    case MODE_RESIDUAL: stage_kernel<DIM, MODE_RESIDUAL><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_STAGE1: stage_kernel<DIM, MODE_STAGE1><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_STAGE2: stage_kernel<DIM, MODE_STAGE2><<<grid, block, smem, st>>>(*tmap, a); break;
+    default: stage_kernel<DIM, MODE_STAGE3><<<grid, block, smem, st>>>(*tmap, a); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t set_stage_attributes_dim(size_t smem) {
+  cudaError_t e = cudaSuccess;
+  const void *k[4] = {(const void *)stage_kernel<DIM, MODE_RESIDUAL>, (const void *)stage_kernel<DIM, MODE_STAGE1>,
+                      (const void *)stage_kernel<DIM, MODE_STAGE2>, (const void *)stage_kernel<DIM, MODE_STAGE3>};
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
+
+}  // namespace fvk

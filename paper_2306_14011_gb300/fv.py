@@ -1,0 +1,292 @@
+"""Python binding of libfv (include/fv.h): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels; this module converts
+torch tensors / numpy arrays to pointers and status codes to exceptions.  It
+never computes anything itself and has no CPU fallback: if libfv cannot be
+built or loaded, or there is no CUDA device, calls raise.
+
+Functions mirror the C ABI one to one (fv_init, fv_residual, fv_time_step,
+fv_rk_step, fv_run, fv_sync, fv_destroy, ...); `Solver` wraps a context.
+State arrays: torch.float64 CUDA tensors (device pointers, stream-ordered) or
+numpy float64 arrays (host pointers: the library stages them and waits).
+Shapes follow the inputs module: (nvar, ny, nx) in 2D, (nvar, nz, ny, nx) in 3D.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+FV_OK, FV_EINVAL, FV_ENOMEM, FV_ECUDA, FV_ENONPHYSICAL, FV_ETIMEOUT, FV_EUNSUPPORTED = range(7)
+FV_BC_PERIODIC, FV_BC_TRANSMISSIVE = 0, 1
+FV_LOADER_TMA, FV_LOADER_PLAIN = 0, 1
+
+
+class FvError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+class fv_grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("len", C.c_double * 3), ("bc", (C.c_int * 2) * 3)]
+
+
+class fv_scheme(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("eps", C.c_double), ("kappa", C.c_double),
+                ("efix", C.c_double)]
+
+
+class fv_kernel_cfg(C.Structure):
+    _fields_ = [("tile", C.c_int * 3), ("threads", C.c_int), ("grid", C.c_int), ("loader", C.c_int)]
+
+
+class fv_launch(C.Structure):
+    _fields_ = [("stage", fv_kernel_cfg * 3), ("dt", fv_kernel_cfg)]
+
+
+_lib = None
+_VP = C.c_void_p
+
+
+def load() -> C.CDLL:
+    """Build (if stale) and load libfv.so from the package's _build folder."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.POINTER
+        L.fv_strerror.argtypes = [C.c_int]
+        L.fv_strerror.restype = C.c_char_p
+        L.fv_default_launch.argtypes = [P(fv_grid), P(fv_launch)]
+        L.fv_init.argtypes = [P(_VP), P(fv_grid), C.c_int, P(fv_scheme), P(fv_launch), _VP]
+        L.fv_set_launch.argtypes = [_VP, P(fv_launch)]
+        L.fv_get_launch.argtypes = [_VP, P(fv_launch)]
+        L.fv_residual.argtypes = [_VP, _VP, _VP, _VP]
+        L.fv_time_step.argtypes = [_VP, _VP, _VP]
+        L.fv_rk_step.argtypes = [_VP, _VP, C.c_double, _VP]
+        L.fv_run.argtypes = [_VP, _VP, C.c_int, C.c_double, _VP]
+        L.fv_sync.argtypes = [_VP]
+        L.fv_destroy.argtypes = [_VP]
+        L.fv_destroy.restype = None
+        L.fv_debug_math.argtypes = [_VP, _VP, _VP, C.c_long, _VP]
+        for name in ("fv_default_launch", "fv_init", "fv_set_launch", "fv_get_launch", "fv_residual",
+                     "fv_time_step", "fv_rk_step", "fv_run", "fv_sync", "fv_debug_math"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def strerror(status: int) -> str:
+    return load().fv_strerror(status).decode()
+
+
+def _check(status: int, where: str):
+    if status != FV_OK:
+        raise FvError(status, where)
+
+
+# ----------------------------------------------------------------------------- marshalling
+
+def make_grid(g) -> fv_grid:
+    G = fv_grid()
+    G.dim = g.dim
+    for a in range(3):
+        G.n[a] = g.n[a] if a < g.dim else 1
+        G.len[a] = g.length[a]
+        G.bc[a][0], G.bc[a][1] = g.bc[a]
+    return G
+
+
+def make_scheme(gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1) -> fv_scheme:
+    return fv_scheme(gamma, cfl, eps, kappa, efix)
+
+
+def launch_to_dict(l: fv_launch) -> dict:
+    st = [dict(tile=tuple(l.stage[s].tile), threads=l.stage[s].threads, loader=l.stage[s].loader) for s in range(3)]
+    return dict(stage=st, dt=dict(threads=l.dt.threads, grid=l.dt.grid))
+
+
+def launch_from_dict(d: dict) -> fv_launch:
+    l = fv_launch()
+    for s in range(3):
+        e = d["stage"][s]
+        for a in range(3):
+            l.stage[s].tile[a] = e["tile"][a]
+        l.stage[s].threads = e["threads"]
+        l.stage[s].grid = 0
+        l.stage[s].loader = e.get("loader", FV_LOADER_TMA)
+    l.dt.threads = d["dt"]["threads"]
+    l.dt.grid = d["dt"].get("grid", 0)
+    return l
+
+
+def _ptr(x) -> int:
+    """Device pointer of a CUDA float64 tensor or host pointer of a numpy array."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise TypeError("numpy arrays must be C-contiguous float64")
+        return x.ctypes.data
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        if not x.is_cuda:
+            return _ptr(x.numpy())
+        return x.data_ptr()
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------------------------- C ABI mirror
+
+def fv_default_launch(g) -> fv_launch:
+    l = fv_launch()
+    _check(load().fv_default_launch(C.byref(make_grid(g)), C.byref(l)), "fv_default_launch")
+    return l
+
+
+def fv_init(g, scheme: fv_scheme, launch: Optional[fv_launch] = None, stream=None) -> int:
+    ctx = _VP()
+    G = make_grid(g)
+    _check(load().fv_init(C.byref(ctx), C.byref(G), 1, C.byref(scheme), C.byref(launch) if launch else None,
+                          _stream_handle(stream)), "fv_init")
+    return ctx.value
+
+
+def fv_set_launch(ctx: int, launch: fv_launch):
+    _check(load().fv_set_launch(ctx, C.byref(launch)), "fv_set_launch")
+
+
+def fv_get_launch(ctx: int) -> fv_launch:
+    l = fv_launch()
+    _check(load().fv_get_launch(ctx, C.byref(l)), "fv_get_launch")
+    return l
+
+
+def fv_residual(ctx: int, U, R, rnorm2=None):
+    _check(load().fv_residual(ctx, _ptr(U), _ptr(R), None if rnorm2 is None else _ptr(rnorm2)), "fv_residual")
+
+
+def fv_time_step(ctx: int, U, dt_out=None) -> Optional[float]:
+    if dt_out is None:
+        d = C.c_double()
+        _check(load().fv_time_step(ctx, _ptr(U), C.addressof(d)), "fv_time_step")
+        return d.value
+    _check(load().fv_time_step(ctx, _ptr(U), _ptr(dt_out)), "fv_time_step")
+    return None
+
+
+def fv_rk_step(ctx: int, U, dt: float = 0.0, want_dt: bool = False) -> Optional[float]:
+    d = C.c_double()
+    _check(load().fv_rk_step(ctx, _ptr(U), float(dt), C.addressof(d) if want_dt else None), "fv_rk_step")
+    return d.value if want_dt else None
+
+
+def fv_run(ctx: int, U, nsteps: int, dt_fixed: float = 0.0, want_time: bool = False) -> Optional[float]:
+    t = C.c_double()
+    _check(load().fv_run(ctx, _ptr(U), int(nsteps), float(dt_fixed), C.addressof(t) if want_time else None),
+           "fv_run")
+    return t.value if want_time else None
+
+
+def fv_sync(ctx: int):
+    _check(load().fv_sync(ctx), "fv_sync")
+
+
+def fv_destroy(ctx: int):
+    load().fv_destroy(ctx)
+
+
+def fv_debug_math(x, out_rsqrt, out_rcp, stream=None):
+    _check(load().fv_debug_math(_ptr(x), _ptr(out_rsqrt), _ptr(out_rcp), x.numel(), _stream_handle(stream)),
+           "fv_debug_math")
+
+
+# ----------------------------------------------------------------------------- convenience wrapper
+
+class Solver:
+    """A libfv context for one grid.
+
+    Solver(grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1,
+           launch=None (dict or fv_launch), stream=None (torch's current stream))
+    """
+
+    def __init__(self, grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, launch=None, stream=None):
+        self.grid = grid
+        self.scheme = make_scheme(gamma, cfl, eps, kappa, efix)
+        if isinstance(launch, dict):
+            launch = launch_from_dict(launch)
+        self.ctx = fv_init(grid, self.scheme, launch, stream)
+
+    # shapes
+    def _chk(self, U):
+        if tuple(U.shape) != tuple(self.grid.shape):
+            raise ValueError(f"state shape {tuple(U.shape)} != grid shape {tuple(self.grid.shape)}")
+
+    @property
+    def launch(self) -> dict:
+        return launch_to_dict(fv_get_launch(self.ctx))
+
+    @launch.setter
+    def launch(self, d):
+        fv_set_launch(self.ctx, launch_from_dict(d) if isinstance(d, dict) else d)
+
+    def residual(self, U, R=None, norms: bool = False):
+        """R_h of Eq. (5); with norms=True also returns sum_cells R_v^2 per variable."""
+        self._chk(U)
+        if R is None:
+            R = U.new_empty(U.shape) if not isinstance(U, np.ndarray) else np.empty_like(U)
+        nrm = None
+        if norms:
+            nrm = np.zeros(self.grid.nvar) if isinstance(U, np.ndarray) else U.new_zeros(self.grid.nvar)
+        fv_residual(self.ctx, U, R, nrm)
+        return (R, nrm) if norms else R
+
+    def time_step(self, U) -> float:
+        self._chk(U)
+        return fv_time_step(self.ctx, U)
+
+    def rk_step(self, U, dt: float = 0.0, return_dt: bool = False):
+        self._chk(U)
+        return fv_rk_step(self.ctx, U, dt, want_dt=return_dt)
+
+    def run(self, U, nsteps: int, dt_fixed: float = 0.0, return_time: bool = False):
+        self._chk(U)
+        return fv_run(self.ctx, U, nsteps, dt_fixed, want_time=return_time)
+
+    def sync(self):
+        fv_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            fv_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,333 @@
+"""GPU parity: libfv kernels (through the C ABI) against the CPU oracle.
+
+Tolerances, relative L-infinity per conserved variable (max|gpu - ref| over
+max|ref|):
+  * states after one SSP-RK3 step: 1e-12; after 100 steps: 1e-9;
+  * residuals: 1e-12, except where cancellation puts the rounding floor of
+    FP64 itself above that: the residual of a variable can be 1e-5 of the
+    fluxes it is the difference of (Kelvin-Helmholtz), and then the FP64
+    oracle's own error against the same definition evaluated in extended
+    precision reaches ~2e-12.  There the bar is 4x that measured oracle error,
+    applied both to GPU - oracle and to GPU - extended precision, i.e. the GPU
+    must be as accurate as the oracle;
+  * exact zero where the oracle's value is exactly zero (free stream).
+Reconstruction is bitwise identical on both sides; the Roe flux differs by
+rounding order (FMA contraction, an algebraically rearranged flux, refined
+reciprocal square roots within 2 ulp).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2306_14011_gb300 import fv  # noqa: E402
+from paper_2306_14011_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL_RES = 1e-12
+TOL_100 = 1e-9
+
+
+def relerr(a, b):
+    """max over variables of max|a_v - b_v| / max|b_v| (exact match needed where b_v == 0)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    worst = 0.0
+    for v in range(b.shape[0]):
+        den = np.abs(b[v]).max()
+        num = np.abs(a[v] - b[v]).max()
+        if den == 0.0:
+            if num != 0.0:
+                return np.inf
+            continue
+        worst = max(worst, num / den)
+    return worst
+
+
+def assert_residual_parity(g, U, R, cells=None, tag=""):
+    """R: GPU residual, full (nvar, ...) array, or (len(cells), nvar) when cells
+    is given.  Checked against the FP64 oracle and its extended-precision
+    evaluation (see the module docstring for the bar)."""
+    if cells is None:
+        Ro = O.residual(g, U).reshape(g.nvar, -1)
+        Rx = O.residual_ext(g, U).reshape(g.nvar, -1)
+        Rg = np.asarray(R).reshape(g.nvar, -1)
+    else:
+        Ro = O.residual_cells(g, U, cells).T
+        Rx = O.residual_cells(g, U, cells, extended=True).T
+        Rg = np.asarray(R).T
+    report = []
+    for v in range(g.nvar):
+        scale = np.abs(Rx[v]).max()
+        e_orc = np.abs(Ro[v] - Rx[v]).max()
+        e_gpu = np.abs(Rg[v] - Rx[v]).max()
+        d = np.abs(Rg[v] - Ro[v]).max()
+        if scale == 0.0:
+            assert d == 0.0 and np.all(Ro[v] == 0.0), (tag, v)
+            continue
+        tol = max(TOL_RES * scale, 4.0 * e_orc)
+        report.append(dict(var=v, rel_gpu_oracle=d / scale, rel_gpu_ext=e_gpu / scale, rel_oracle_ext=e_orc / scale))
+        assert d <= tol, (tag, v, d / scale, e_orc / scale)
+        assert e_gpu <= tol, (tag, v, e_gpu / scale, e_orc / scale)
+    path = os.environ.get("FV_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"case": tag, "vars": report}) + "\n")
+
+
+def dev(U):
+    return torch.from_numpy(np.ascontiguousarray(U)).cuda()
+
+
+def launch_with(g, tile=None, threads=256, loader=fv.FV_LOADER_TMA):
+    d = fv.launch_to_dict(fv.fv_default_launch(g))
+    for s in range(3):
+        if tile is not None:
+            d["stage"][s]["tile"] = tile
+        d["stage"][s]["threads"] = threads
+        d["stage"][s]["loader"] = loader
+    return d
+
+
+CASES = {
+    "vortex128": lambda: I.isentropic_vortex(128, seed=0),
+    "kh256": lambda: I.kelvin_helmholtz(256, seed=1),
+    "sod_rot64_transmissive": lambda: I.sod_rotated(64, 0.7),
+    "tiny4x4": lambda: (I.grid2d(4, 4, 1.0, 1.0), I.random_smooth(I.grid2d(4, 4, 1.0, 1.0), seed=1)),
+    "odd5x7": lambda: (I.grid2d(5, 7, 1.0, 1.4), I.random_smooth(I.grid2d(5, 7, 1.0, 1.4), seed=2)),
+    "ragged34x18": lambda: (I.grid2d(34, 18, 1.0, 0.5), I.random_smooth(I.grid2d(34, 18, 1.0, 0.5), seed=3)),
+    "ragged70x45_mixed_bc": lambda: (I.grid2d(70, 45, 1.0, 0.7, ((1, 1), (0, 0), (0, 0))),
+                                     I.random_smooth(I.grid2d(70, 45, 1.0, 0.7, ((1, 1), (0, 0), (0, 0))), seed=4)),
+    "tgv24": lambda: I.taylor_green(24, seed=2),
+    "box3d_10x7x9_transmissive": lambda: (I.grid3d(10, 7, 9, 1.0, 0.7, 0.9, I.BC_TRANSMISSIVE),
+                                          I.random_smooth(I.grid3d(10, 7, 9, 1.0, 0.7, 0.9, I.BC_TRANSMISSIVE),
+                                                          seed=5)),
+    "box3d_36x20x14_mixed": lambda: (I.grid3d(36, 20, 14, 1.0, 0.6, 0.5, ((0, 0), (1, 1), (0, 0))),
+                                     I.random_smooth(I.grid3d(36, 20, 14, 1.0, 0.6, 0.5, ((0, 0), (1, 1), (0, 0))),
+                                                     seed=6)),
+}
+
+
+@pytest.mark.parametrize("loader", [fv.FV_LOADER_TMA, fv.FV_LOADER_PLAIN])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_residual_matches_oracle(case, loader):
+    g, U = CASES[case]()
+    with fv.Solver(g, launch=launch_with(g, loader=loader)) as s:
+        R = s.residual(dev(U)).cpu().numpy()
+    assert_residual_parity(g, U, R, tag=f"{case}-loader{loader}")
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_free_stream_residual_is_exactly_zero(dim):
+    g = I.grid2d(66, 40, 1.0, 2.0) if dim == 2 else I.grid3d(20, 18, 12, 1.0, 2.0, 3.0)
+    U = I.uniform_state(g)
+    with fv.Solver(g) as s:
+        R = s.residual(dev(U)).cpu().numpy()
+        Ud = dev(U)
+        s.rk_step(Ud)
+        assert np.array_equal(Ud.cpu().numpy(), U)
+    assert np.all(R == 0.0)
+
+
+@pytest.mark.parametrize("case", ["vortex128", "kh256", "sod_rot64_transmissive", "tgv24", "odd5x7"])
+def test_time_step_matches_oracle(case):
+    g, U = CASES[case]()
+    with fv.Solver(g) as s:
+        dt = s.time_step(dev(U))
+        dtd = torch.zeros(1, dtype=torch.float64, device="cuda")
+        fv.fv_time_step(s.ctx, dev(U), dtd)
+        torch.cuda.synchronize()
+    dto = O.time_step(g, U)
+    assert abs(dt - dto) <= 2e-15 * dto
+    assert dtd.item() == dt
+
+
+@pytest.mark.parametrize("case", ["vortex128", "kh256", "sod_rot64_transmissive", "ragged70x45_mixed_bc", "tgv24",
+                                  "box3d_36x20x14_mixed"])
+@pytest.mark.parametrize("cfl_dt", [False, True])
+def test_rk_step_matches_oracle(case, cfl_dt):
+    g, U = CASES[case]()
+    dto = O.time_step(g, U)
+    Uo, _ = O.rk3_step(g, U, dto)
+    with fv.Solver(g) as s:
+        Ud = dev(U)
+        used = s.rk_step(Ud, 0.0 if cfl_dt else dto, return_dt=True)
+        U1 = Ud.cpu().numpy()
+    assert abs(used - dto) <= 2e-15 * dto
+    assert relerr(U1, Uo) <= TOL_RES
+
+
+def test_config1_vortex_100_steps_matches_oracle():
+    """128x128 periodic vortex + seeded density noise, CFL 0.5, 100 steps."""
+    g, U = I.isentropic_vortex(128, seed=0)
+    Uo, to = O.run(g, U, 100)
+    with fv.Solver(g) as s:
+        Ud = dev(U)
+        t = s.run(Ud, 100, return_time=True)
+        U100 = Ud.cpu().numpy()
+    assert abs(t - to) <= 1e-12 * to
+    assert relerr(U100, Uo) <= TOL_100
+
+
+def test_residual_norms_match_oracle():
+    g, U = I.kelvin_helmholtz(256, seed=1)
+    Ro = O.residual(g, U)
+    ref = (Ro.reshape(g.nvar, -1) ** 2).sum(axis=1)
+    with fv.Solver(g) as s:
+        R, nrm = s.residual(dev(U), norms=True)
+        _, nrm_host = s.residual(U.copy(), norms=True)
+    # the sums of squares of the GPU's own residual, in a fixed order, agree
+    # with the oracle's up to the residual parity above (squared)
+    own = (R.cpu().numpy().reshape(g.nvar, -1) ** 2).sum(axis=1)
+    assert np.max(np.abs(nrm.cpu().numpy() - own) / own) <= 1e-13
+    assert np.max(np.abs(nrm.cpu().numpy() - ref) / ref) <= 1e-10
+    assert np.array_equal(nrm.cpu().numpy(), nrm_host)
+
+
+def test_host_pointer_path_equals_device_path():
+    g, U = I.isentropic_vortex(96, seed=3)
+    with fv.Solver(g) as s:
+        Rd = s.residual(dev(U)).cpu().numpy()
+        Rh = s.residual(U.copy())
+        assert np.array_equal(Rd, Rh)
+        Ud = dev(U)
+        s.run(Ud, 5)
+        Uh = U.copy()
+        s.run(Uh, 5)
+        assert np.array_equal(Ud.cpu().numpy(), Uh)
+
+
+def test_graph_replay_equals_single_steps():
+    g, U = I.kelvin_helmholtz(128, seed=1)
+    with fv.Solver(g) as s:
+        A = dev(U)
+        s.run(A, 37)
+        B = dev(U)
+        for _ in range(37):
+            s.rk_step(B)
+        assert torch.equal(A, B)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_launch_configuration_does_not_change_results(dim):
+    """Every face flux is computed from the same operands whatever the tile, so
+    results are bitwise independent of the launch configuration."""
+    if dim == 2:
+        g, U = I.kelvin_helmholtz(160, seed=1)
+        cfgs = [((32, 16, 1), 256), ((16, 8, 1), 64), ((64, 4, 1), 128), ((8, 32, 1), 96), ((2, 2, 1), 32),
+                ((128, 2, 1), 256)]
+    else:
+        g, U = I.taylor_green(20, seed=2)
+        cfgs = [((16, 8, 4), 256), ((8, 8, 8), 128), ((4, 4, 2), 32), ((20, 4, 2), 160)]
+    outs = []
+    for tile, thr in cfgs:
+        for loader in (fv.FV_LOADER_TMA, fv.FV_LOADER_PLAIN):
+            with fv.Solver(g, launch=launch_with(g, tile=tile, threads=thr, loader=loader)) as s:
+                R = s.residual(dev(U))
+                Ud = dev(U)
+                s.run(Ud, 3)
+                outs.append((R.cpu().numpy(), Ud.cpu().numpy()))
+    for R, Un in outs[1:]:
+        assert np.array_equal(R, outs[0][0])
+        assert np.array_equal(Un, outs[0][1])
+
+
+def test_non_physical_state_is_reported():
+    g, U = I.isentropic_vortex(64, seed=0)
+    U[0, 10, 20] = -0.5
+    with fv.Solver(g) as s:
+        with pytest.raises(fv.FvError) as e:
+            s.time_step(dev(U))
+        assert e.value.status == fv.FV_ENONPHYSICAL
+        # flags are cleared once reported
+        s.sync()
+        with pytest.raises(fv.FvError) as e:
+            s.run(dev(U), 2, return_time=True)
+        assert e.value.status == fv.FV_ENONPHYSICAL
+
+
+def test_invalid_launch_is_rejected():
+    g, U = I.isentropic_vortex(64)
+    for bad in [dict(tile=(3, 8, 1)), dict(tile=(32, 16, 2)), dict(threads=48), dict(threads=512),
+                dict(tile=(252, 252, 1))]:
+        d = launch_with(g)
+        for s_ in range(3):
+            d["stage"][s_].update(bad)
+        with pytest.raises(fv.FvError) as e:
+            fv.Solver(g, launch=d)
+        assert e.value.status == fv.FV_EINVAL
+
+
+def test_refined_rsqrt_and_reciprocal_are_within_two_ulp():
+    rng = np.random.default_rng(0)
+    x = np.exp2(rng.uniform(-300, 300, 1 << 20)) * rng.uniform(1, 2, 1 << 20)
+    xd = dev(x)
+    a = torch.empty_like(xd)
+    b = torch.empty_like(xd)
+    fv.fv_debug_math(xd, a, b)
+    torch.cuda.synchronize()
+    rs_ref = 1.0 / np.sqrt(x)
+    rc_ref = 1.0 / x
+    assert np.max(np.abs(a.cpu().numpy() - rs_ref) / np.spacing(rs_ref)) <= 2.0
+    assert np.max(np.abs(b.cpu().numpy() - rc_ref) / np.spacing(rc_ref)) <= 2.0
+
+
+# ----------------------------------------------------------------------------- full-size workloads
+
+def _sample_cells(g, rng, k):
+    n = g.n
+    cells = list(rng.integers(0, g.ncells, k))
+    # domain corners and edges, and cells around tile boundaries of the default launch
+    for x in (0, 1, 2, 15, 16, 31, 32, 33, n[0] - 2, n[0] - 1):
+        for y in (0, 1, 15, 16, 17, n[1] - 2, n[1] - 1):
+            if g.dim == 2:
+                cells.append(y * n[0] + x)
+            else:
+                for z in (0, 3, 4, n[2] - 1):
+                    cells.append((z * n[1] + y) * n[0] + x)
+    return np.unique(np.array(cells, dtype=np.int64))
+
+
+def test_fullsize_kh4096_residual_and_step_sampled():
+    """Kelvin-Helmholtz 4096x4096 (the benchmark workload, default launch):
+    residual on sampled cells, and one CFL SSP-RK3 step checked cell by cell on
+    periodic windows the oracle advances with its own dt."""
+    g, U = I.kelvin_helmholtz(4096, seed=1)
+    rng = np.random.default_rng(0)
+    cells = _sample_cells(g, rng, 3000)
+    with fv.Solver(g) as s:
+        Ud = dev(U)
+        R = s.residual(Ud).cpu().numpy().reshape(g.nvar, -1)[:, cells].T
+        assert_residual_parity(g, U, R, cells, tag="kh4096-sampled")
+        dto = O.time_step(g, U)
+        used = s.rk_step(Ud, 0.0, return_dt=True)
+        assert abs(used - dto) <= 2e-15 * dto
+        U1 = Ud.cpu().numpy()
+    W = 8  # three stages widen the dependence cone by 6 cells; the window edge stays 2 cells clear
+    h = 1.0 / 4096
+    gw = I.grid2d(2 * W + 1, 2 * W + 1, (2 * W + 1) * h, (2 * W + 1) * h)
+    pick = rng.choice(cells, 400, replace=False)
+    scale = np.abs(U1.reshape(g.nvar, -1)).max(axis=1)
+    for c in pick:
+        y, x = divmod(int(c), 4096)
+        iy = (np.arange(y - W, y + W + 1)) % 4096
+        ix = (np.arange(x - W, x + W + 1)) % 4096
+        Uw = np.ascontiguousarray(U[:, iy][:, :, ix])
+        Uw1, _ = O.rk3_step(gw, Uw, dto)
+        got = U1[:, y, x]
+        exp = Uw1[:, W, W]
+        assert np.all(np.abs(got - exp) <= TOL_RES * scale), (c, got, exp)
+
+
+def test_fullsize_tgv384_residual_sampled():
+    g, U = I.taylor_green(384, seed=2)
+    rng = np.random.default_rng(1)
+    cells = _sample_cells(g, rng, 3000)
+    with fv.Solver(g) as s:
+        R = s.residual(dev(U)).cpu().numpy().reshape(g.nvar, -1)[:, cells].T
+    assert_residual_parity(g, U, R, cells, tag="tgv384-sampled")

@@ -1,0 +1,83 @@
+"""CPU-only checks of the C-ABI library: it builds for sm_103a, loads, and
+exports every entry point include/fv.h declares; host-side validation works
+without a GPU.  No kernel is launched here."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2306_14011_gb300 import fv
+from paper_2306_14011_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(fv_\w+)\s*\(", txt, re.M))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = fv.load()
+    names = _declared()
+    assert "fv_run" in names and "fv_init" in names and len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", fv.library_path()], capture_output=True, text=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}\b", out), n
+
+
+def test_library_targets_sm_103a_only():
+    out = subprocess.run(["cuobjdump", "--list-elf", fv.library_path()], capture_output=True, text=True).stdout
+    arches = set(re.findall(r"sm_\d+a?", out))
+    assert arches == {"sm_103a"}, arches
+
+
+def test_strerror_and_default_launch_without_gpu():
+    assert fv.strerror(fv.FV_EINVAL) == "invalid argument"
+    assert fv.strerror(99) == "unknown status"
+    l2 = fv.fv_default_launch(I.grid2d(64, 64, 1.0, 1.0))
+    assert tuple(l2.stage[0].tile) == (32, 16, 1) and l2.stage[0].threads == 256
+    l3 = fv.fv_default_launch(I.grid3d(16, 16, 16, 1.0, 1.0, 1.0))
+    assert tuple(l3.stage[2].tile) == (16, 8, 4)
+
+
+def test_invalid_grids_are_rejected_on_the_host():
+    bad = [
+        I.GridSpec(4, (8, 8, 1), (1.0, 1.0, 1.0)),          # dim
+        I.GridSpec(2, (0, 8, 1), (1.0, 1.0, 1.0)),          # empty axis
+        I.GridSpec(2, (8, 8, 1), (1.0, -1.0, 1.0)),         # length
+        I.GridSpec(2, (8, 8, 1), (1.0, 1.0, 1.0), ((0, 1), (0, 0), (0, 0))),  # half-periodic axis
+    ]
+    for g in bad:
+        with pytest.raises(fv.FvError) as e:
+            fv.fv_default_launch(g)
+        assert e.value.status == fv.FV_EINVAL
+    lib = fv.load()
+    G = fv.make_grid(I.grid2d(8, 8, 1.0, 1.0))
+    G.n[2] = 2  # nz != 1 in 2D
+    assert lib.fv_default_launch(C.byref(G), C.byref(fv.fv_launch())) == fv.FV_EINVAL
+    # null context pointers are rejected before any CUDA call
+    assert lib.fv_sync(None) == fv.FV_EINVAL
+    assert lib.fv_residual(None, None, None, None) == fv.FV_EINVAL
+    assert lib.fv_run(None, None, 1, 0.0, None) == fv.FV_EINVAL
+
+
+def test_init_without_a_gpu_reports_an_error_not_a_crash():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = fv.load()
+    ctx = C.c_void_p()
+    G = fv.make_grid(I.grid2d(8, 8, 1.0, 1.0))
+    S = fv.make_scheme()
+    st = lib.fv_init(C.byref(ctx), C.byref(G), 1, C.byref(S), None, None)
+    assert st in (fv.FV_ECUDA, fv.FV_ENOMEM)
+    assert not ctx.value

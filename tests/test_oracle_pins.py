@@ -171,6 +171,27 @@ def test_entropy_fix_only_acts_near_sonic_points():
     assert np.abs(f2 - f1).max() < 1e-7
 
 
+def test_entropy_fix_is_continuous_at_its_threshold():
+    """Harten's |lambda|* = (lambda^2 + delta^2) / (2 delta) meets |lambda| at
+    |lambda| = delta, so the flux is continuous as delta crosses |lambda|."""
+    c = np.sqrt(G)
+    QL = _state(1.0, [c - 0.05, 0.0], 1.0)
+    QR = _state(0.97, [c - 0.02, 0.0], 0.96)
+    # Roe state of this pair: |u~ - c~| / c~ is the efix at which the fix switches on
+    dim = 2
+    A = _jacobian(_roe_state(QL, QR, dim), 0, dim)
+    lam = np.sort(np.linalg.eigvals(A).real)
+    ct = 0.5 * (lam[-1] - lam[0])
+    e_star = abs(lam[0]) / ct
+    lo = O.roe_flux(QL, QR, 0, 2, O.scheme(efix=e_star * (1 - 1e-9)))
+    hi = O.roe_flux(QL, QR, 0, 2, O.scheme(efix=e_star * (1 + 1e-9)))
+    off = O.roe_flux(QL, QR, 0, 2, O.scheme(efix=0.0))
+    assert np.abs(hi - lo).max() < 1e-9
+    np.testing.assert_allclose(lo, off, rtol=0, atol=1e-9)
+    far = O.roe_flux(QL, QR, 0, 2, O.scheme(efix=4 * e_star))
+    assert np.abs(far - off).max() > 1e-5
+
+
 # ------------------------------------------------------------------ MUSCL / minmod, Eq. (6)
 
 def test_muscl_is_exact_on_linear_data_and_kappa_free_with_minmod():
@@ -336,3 +357,23 @@ def test_dual_number_jvp_matches_central_differences():
     h = 1e-6
     fd = (O.residual(g, U + h * dU) - O.residual(g, U - h * dU)) / (2 * h)
     np.testing.assert_allclose(dR, fd, rtol=0, atol=1e-6 * np.abs(dR).max())
+
+
+# ------------------------------------------------------------------ rounding floor of FP64 evaluations
+
+def test_fp64_oracle_is_within_rounding_of_extended_precision():
+    """The FP64 residual against the same definition evaluated in long double:
+    ~1e-14 of max|R_v| on the vortex, but ~1e-12 on Kelvin-Helmholtz, where
+    the residual of some variables is ~1e-5 of the fluxes it is a difference
+    of.  This measured floor sets the residual parity bar of the GPU tests."""
+    g, U = I.isentropic_vortex(64, seed=0)
+    R, Rx = O.residual(g, U), O.residual_ext(g, U)
+    for v in range(g.nvar):
+        assert np.abs(R[v] - Rx[v]).max() <= 1e-13 * np.abs(Rx[v]).max()
+    g, U = I.kelvin_helmholtz(128, seed=1)
+    R, Rx = O.residual(g, U), O.residual_ext(g, U)
+    worst = max(np.abs(R[v] - Rx[v]).max() / np.abs(Rx[v]).max() for v in range(g.nvar))
+    assert 1e-14 < worst < 1e-10
+    # extended precision is the same definition: it reproduces free-stream zeros
+    gz = I.grid2d(9, 6, 1.0, 1.0)
+    assert np.all(O.residual_ext(gz, I.uniform_state(gz)) == 0.0)
