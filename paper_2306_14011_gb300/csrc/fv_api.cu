@@ -91,6 +91,10 @@ struct fv_ctx {
 
 namespace {
 
+// Shared memory the stage kernels declare statically (the residual kernel's
+// norm reduction buffer, 5 x 32 doubles), kept free of the dynamic budget.
+constexpr size_t kStaticSmemReserve = 2048;
+
 int validate_grid(const fv_grid *g) {
   if (!g || (g->dim != 2 && g->dim != 3)) return FV_EINVAL;
   for (int d = 0; d < 3; ++d) {
@@ -129,7 +133,7 @@ int validate_launch(const fv_grid *g, const fv_launch *l, size_t smem_optin) {
     if (k.threads < 32 || k.threads > 256 || k.threads % 32) return FV_EINVAL;
     if (k.grid != 0) return FV_EINVAL;  // tiled kernels cover the domain
     if (k.loader != FV_LOADER_TMA && k.loader != FV_LOADER_PLAIN) return FV_EINVAL;
-    if (stage_smem_bytes(g->dim, k.tile) > smem_optin) return FV_EINVAL;
+    if (stage_smem_bytes(g->dim, k.tile) + kStaticSmemReserve > smem_optin) return FV_EINVAL;
   }
   if (l->dt.threads < 32 || l->dt.threads > 1024 || l->dt.threads % 32 || l->dt.grid < 0) return FV_EINVAL;
   return FV_OK;
@@ -259,12 +263,7 @@ int read_flags(fv_ctx *c) {
 }
 
 int set_attributes(fv_ctx *c) {
-  size_t mx = 0;
-  for (int s = 0; s < 3; ++s) {
-    const size_t b = stage_smem_bytes(c->grid.dim, c->launch.stage[s].tile);
-    mx = b > mx ? b : mx;
-  }
-  FV_CK(stage_kernel_attributes(c->grid.dim, mx));
+  FV_CK(stage_kernel_attributes(c->grid.dim, c->smem_optin));
   return FV_OK;
 }
 

@@ -313,13 +313,22 @@ cudaError_t launch_stage_dim(int mode, const CUtensorMap *tmap, const StageArgs 
   return cudaGetLastError();
 }
 
+// Allow each stage kernel the largest dynamic shared memory the device offers
+// (opt-in limit minus the kernel's static shared memory), so contexts with
+// different tile shapes never lower each other's limit.  `smem_optin` is the
+// device's per-block opt-in limit.
 template <int DIM>
-cudaError_t set_stage_attributes_dim(size_t smem) {
+cudaError_t set_stage_attributes_dim(size_t smem_optin) {
   cudaError_t e = cudaSuccess;
   const void *k[4] = {(const void *)stage_kernel<DIM, MODE_RESIDUAL>, (const void *)stage_kernel<DIM, MODE_STAGE1>,
                       (const void *)stage_kernel<DIM, MODE_STAGE2>, (const void *)stage_kernel<DIM, MODE_STAGE3>};
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
-    e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k[i]);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(smem_optin - fa.sharedSizeBytes));
+  }
   return e;
 }
 

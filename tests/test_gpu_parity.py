@@ -331,3 +331,18 @@ def test_fullsize_tgv384_residual_sampled():
     with fv.Solver(g) as s:
         R = s.residual(dev(U)).cpu().numpy().reshape(g.nvar, -1)[:, cells].T
     assert_residual_parity(g, U, R, cells, tag="tgv384-sampled")
+
+
+def test_contexts_with_different_tile_shapes_coexist():
+    """A context with small tiles must not lower the shared-memory limit a
+    context with large tiles relies on (kernel attributes are process-wide)."""
+    g, U = I.kelvin_helmholtz(128, seed=1)
+    big = fv.Solver(g, launch=launch_with(g, tile=(64, 32, 1)))
+    small = fv.Solver(g, launch=launch_with(g, tile=(8, 4, 1), threads=64))
+    try:
+        Rb = big.residual(dev(U)).cpu().numpy()
+        Rs = small.residual(dev(U)).cpu().numpy()
+        assert np.array_equal(Rb, Rs)
+    finally:
+        big.close()
+        small.close()
