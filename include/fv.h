@@ -150,6 +150,32 @@ void fv_destroy(fv_ctx *ctx);
 /* Static description of a status code. */
 const char *fv_strerror(int status);
 
+/* Residual R_h of Eq. (5) and, if rnorm2 != NULL, sum over cells of R_v^2 per
+ * variable -- the same values as fv_residual -- without a context and without
+ * allocating anything.  The paper has no counterpart: this is a facility for
+ * callers that cannot allocate device memory when they call (code running
+ * while a stream is being captured, where cudaMalloc is not allowed; services
+ * that fix their device-memory budget at start-up; hosts that cannot afford
+ * the device-wide synchronisation cudaFree implies).
+ * U, R (nvar*ncells doubles, R not aliasing U) and rnorm2 (nvar doubles) are
+ * caller-owned DEVICE pointers; host pointers return FV_EINVAL.  The default
+ * launch configuration is used, with plain tile loads.  Stream-ordered on
+ * `stream` (a cudaStream_t, NULL = legacy default); returns without waiting.
+ * Scratch: a fixed array of 131072 + 32 doubles (1 MiB + 256 B) in the
+ * library's device image -- every GPU that loads libfv holds it until the
+ * process exits -- holding nvar partial sums per tile.  With rnorm2 != NULL
+ * the grid may have at most 131072 / nvar default tiles (2D: 32768 tiles of
+ * 32x16 cells, e.g. 4096 x 4096; 3D: 26214 tiles of 16x8x4 cells); larger
+ * grids return FV_EINVAL before anything is launched.  The first call on each
+ * device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * and sets kernel attributes: make that first call before any stream capture.
+ * Every call reuses the same scratch (the flags word is cleared by each call,
+ * the partials are rewritten), so calls that may overlap on the GPU -- on
+ * different streams without ordering, or from several threads -- race and
+ * must be serialised by the caller. */
+int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const double *U, double *R, double *rnorm2,
+                        void *stream);
+
 /* Diagnostic of the device arithmetic used by the kernels: for n inputs x
  * (device pointer), out_rsqrt[i] = 1/sqrt(x[i]) and out_rcp[i] = 1/x[i] as
  * computed inside the flux kernels (approximation refined to full double

@@ -74,6 +74,8 @@ def load() -> C.CDLL:
         L.fv_destroy.argtypes = [_VP]
         L.fv_destroy.restype = None
         L.fv_debug_math.argtypes = [_VP, _VP, _VP, C.c_long, _VP]
+        L.fv_residual_noalloc.argtypes = [P(fv_grid), P(fv_scheme), _VP, _VP, _VP, _VP]
+        L.fv_residual_noalloc.restype = C.c_int
         for name in ("fv_default_launch", "fv_init", "fv_set_launch", "fv_get_launch", "fv_residual",
                      "fv_time_step", "fv_rk_step", "fv_run", "fv_sync", "fv_debug_math"):
             getattr(L, name).restype = C.c_int
@@ -212,6 +214,17 @@ def fv_sync(ctx: int):
 
 def fv_destroy(ctx: int):
     load().fv_destroy(ctx)
+
+
+def fv_residual_noalloc(g, scheme: fv_scheme, U, R, rnorm2=None, stream=None):
+    """Residual (and norms) without a context and without allocating: for
+    callers that cannot allocate device memory when they call (e.g. while a
+    stream is being captured).  Device tensors only; grids above the fixed
+    scratch limit raise FvError(FV_EINVAL).  Calls sharing the GPU must not
+    overlap (they share one scratch array)."""
+    _check(load().fv_residual_noalloc(C.byref(make_grid(g)), C.byref(scheme), _ptr(U), _ptr(R),
+                                      None if rnorm2 is None else _ptr(rnorm2), _stream_handle(stream)),
+           "fv_residual_noalloc")
 
 
 def fv_debug_math(x, out_rsqrt, out_rcp, stream=None):
