@@ -101,14 +101,25 @@ typedef struct fv_ctx fv_ctx;
  * and thread count for all stages).  Returns FV_EINVAL for a bad grid. */
 int fv_default_launch(const fv_grid *g, fv_launch *l);
 
-/* Create a solver context for ngrids grids (ngrids = 1; batched grids return
- * FV_EUNSUPPORTED).  Allocates the RK stage buffers and reduction scratch on
- * the current CUDA device.  stream: a cudaStream_t on which every later call
+/* Create a solver context for ngrids grids.  ngrids = 1: one grid, 2D or 3D.
+ * ngrids > 1: a batch of independent 2D grids of any sizes (3D batches return
+ * FV_EUNSUPPORTED), stored packed (see fv_layout) and advanced together by
+ * fv_run / fv_rk_step in one persistent cooperative kernel launch per call,
+ * each grid with its own CFL time step; the batch uses launch stage[0]'s tile
+ * and threads for every stage.  fv_residual and fv_time_step need ngrids = 1.
+ * Allocates the RK stage buffers and reduction scratch on the current CUDA
+ * device.  stream: a cudaStream_t on which every later call
  * is ordered (NULL = the legacy default stream).  l = NULL selects
  * fv_default_launch.  On success *out owns the context (free with
  * fv_destroy). */
 int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, const fv_launch *l,
             void *stream);
+
+/* Layout of the packed state of a context: grid g's SoA block (nvar x cells
+ * doubles, the layout above) starts at offsets[g] doubles; offsets[ngrids] is
+ * the total.  offsets: host array of ngrids + 1 entries.  Blocks start on
+ * 256-byte boundaries. */
+int fv_layout(const fv_ctx *ctx, long long *offsets, int ngrids);
 
 /* Replace / read the launch configuration (validated against the device). */
 int fv_set_launch(fv_ctx *ctx, const fv_launch *l);
@@ -136,8 +147,10 @@ int fv_rk_step(fv_ctx *ctx, double *U, double dt, double *dt_used);
 /* nsteps SSP-RK3 steps in place, replayed from CUDA graphs captured on the
  * first call for this U pointer and dt mode.  dt_fixed > 0 holds the step;
  * otherwise every step takes the CFL step of its starting state.  t_out:
- * NULL (asynchronous) or a host pointer receiving the simulated time (the
- * call waits and reports device-side flags). */
+ * NULL (asynchronous) or a host pointer receiving the simulated time -- one
+ * double per grid (ngrids of them) -- (the call waits and reports device-side
+ * flags).  Batched contexts: U is the packed state, and a grid barrier that
+ * waits longer than 2 s ends the kernel with FV_ETIMEOUT. */
 int fv_run(fv_ctx *ctx, double *U, int nsteps, double dt_fixed, double *t_out);
 
 /* Wait for all work of the context and report (then clear) device-side
@@ -149,6 +162,89 @@ void fv_destroy(fv_ctx *ctx);
 
 /* Static description of a status code. */
 const char *fv_strerror(int status);
+
+/* ------------------------------------------------------------------------
+ * Autotuning (paper Sec. 3.3-3.6): a fully connected network regresses the
+ * run time of one SSP-RK3 step on the launch parameters of the kernels, is
+ * trained on a random sample of the tuning space, and picks the
+ * configuration to use.
+ * ---------------------------------------------------------------------- */
+
+/* Training hyperparameters (Table "para-setting"): L2 coefficient alpha
+ * (1e-4), Adam beta1 (0.95), beta2 (0.90), learning rate (0.0009), numerical
+ * stability eps (1e-9), tolerance tol (1e-6) with n_iter_no_change (10)
+ * epochs, batch (200), max_epochs (200). */
+typedef struct fv_mlp_hyper {
+  double alpha, beta1, beta2, lr, eps, tol;
+  int batch, max_epochs, n_iter_no_change;
+} fv_mlp_hyper;
+
+/* Train the surrogate network on the device, FP64.  nl weight layers with
+ * widths sizes[0..nl] (sizes[0] = features, sizes[nl] = 1, each <= 1024,
+ * nl <= 8): ReLU hidden layers, identity output.  params: device array packed
+ * [W_0 (sizes[0] x sizes[1], row-major), b_0, W_1, b_1, ...], updated in
+ * place.  X: device [n][sizes[0]]; y: device [n]; order: device int32
+ * [epochs][n], the sample indices of each epoch, taken in minibatches of
+ * h->batch.  Loss per minibatch: 1/2 mean (y_hat - y)^2 + alpha/(2B) sum W^2;
+ * Adam with bias corrections; stops early once the epoch loss has not
+ * improved by h->tol for more than h->n_iter_no_change epochs (0 = never).
+ * loss_out: NULL or a host array [epochs] of mean epoch losses; *epochs_run:
+ * epochs done.  Allocates its workspace, waits for completion. */
+int fv_mlp_train(int nl, const int *sizes, double *params, const double *X, const double *y, long n,
+                 const int *order, int epochs, const fv_mlp_hyper *h, double *loss_out, int *epochs_run,
+                 void *stream);
+
+/* out[i] = network output for row i of X (device [n][sizes[0]]), out device [n]. */
+int fv_mlp_predict(int nl, const int *sizes, const double *params, const double *X, long n, double *out,
+                   void *stream);
+
+/* Tuning options; zero fields take the defaults in brackets. */
+typedef struct fv_tune_opts {
+  int samples;     /* random configurations timed, split 75% train / 25% test [400] */
+  int steps;       /* SSP-RK3 steps timed per measurement, after one warm-up step [2] */
+  int repeats;     /* measurements per configuration, median taken [1] */
+  int candidates;  /* random configurations scored by the network [200000] */
+  int top;         /* best-predicted candidates re-measured [16] */
+  int exhaustive;  /* 1: also time every configuration of the reduced space [0] */
+  int final_repeats; /* repeats of the final default / tuned / exhaustive timings [5] */
+  int rounds;      /* surrogate rounds: retrain on all measurements, re-measure the top predictions [3] */
+  int refine;      /* coordinate-descent sweeps around the best measured configuration [2]; -1: none */
+  unsigned long long seed; /* SplitMix64 seed [1] */
+  int hidden[4];   /* hidden-layer widths, 0-terminated; all 0 = (128, 64, 32) */
+  fv_mlp_hyper mlp;
+} fv_tune_opts;
+
+typedef struct fv_tune_report {
+  double t_default;       /* s per SSP-RK3 step, default launch */
+  double t_tuned;         /* s per step, the returned launch */
+  double t_best_sampled;  /* s per step, best of the random sample */
+  double t_exhaustive;    /* s per step, best of the reduced space (0 if not run) */
+  double r2_train, r2_test; /* Eq. (7) on run times, training / held-out samples */
+  double space_size;      /* points in the full tuning space */
+  int n_params;           /* tuning parameters (14 in 2D, 17 in 3D) */
+  int n_train, n_test, epochs, n_measured, n_exhaustive;
+  int rounds, n_refined;  /* surrogate rounds run; measurements made by the refinement */
+  fv_launch exhaustive_best;
+} fv_tune_report;
+
+/* Tune the launch configuration of ctx for the state U (device or host; not
+ * modified: timing runs on a copy in the context's staging buffer).  The space:
+ * per RK-stage kernel tile_x in {8,16,32,64,128}, tile_y in {2,4,8,16,32}
+ * (3D: tile_x {8,16,32}, tile_y {4,8,16}, tile_z {2,4,8}), threads in
+ * {64,96,...,256}, loader in {TMA, plain}; time-step kernel threads in
+ * {128,256,512,1024} and grid in {1,2,4,8} x SMs.  Procedure: time
+ * opts->samples random valid configurations; train the network (features
+ * standardised, target log time standardised); score opts->candidates random
+ * configurations; re-measure the opts->top best predicted; repeat for
+ * opts->rounds rounds, each retrained on everything measured so far (the
+ * held-out 25% of the first sample excepted); then refine the best measured
+ * configuration by coordinate descent (each parameter in turn over its value
+ * set); return the fastest measured configuration in *best (and install it in
+ * ctx).  Features are log2 of the power-of-two parameters.  With
+ * opts->exhaustive, every configuration with one shared (tile, threads) for
+ * the three stages, TMA loads and the default time-step kernel is timed as the
+ * judge.  rep may be NULL.  Waits for completion. */
+int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *best, fv_tune_report *rep);
 
 /* Residual R_h of Eq. (5) and, if rnorm2 != NULL, sum over cells of R_v^2 per
  * variable -- the same values as fv_residual -- without a context and without

@@ -2,6 +2,7 @@
 // validation, TMA tensor maps, host-pointer staging and the CUDA-graph step
 // driver.  Every numerical step runs in the kernels of fv_stage*.cu and
 // fv_reduce.cu.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -87,6 +88,16 @@ struct fv_ctx {
   double *norm_part;          // scratch: per-CTA partials (lazy)
   long long norm_part_cap;
   std::vector<GraphEntry> graphs;
+  // batched contexts (ngrids > 1)
+  int ngrids;
+  std::vector<fv_grid> grids;
+  std::vector<long long> offsets;  // ngrids + 1, in doubles
+  BatchProblem *b_prob;
+  int *b_tile_begin, *b_chunk_begin;
+  unsigned long long *b_smax;      // [2][ngrids]
+  double *b_tacc;                  // [ngrids]
+  unsigned *b_bar;                 // count, generation
+  int b_total_tiles, b_total_chunks, b_blocks;
 };
 
 namespace {
@@ -274,6 +285,188 @@ void drop_graphs(fv_ctx *c) {
 
 }  // namespace
 
+namespace {
+
+constexpr long long kBatchChunk = 4096;  // cells per time-step work item
+
+// Device tables of a batch for the current launch tile; cooperative grid size.
+int batch_setup(fv_ctx *c) {
+  const int *tile = c->launch.stage[0].tile;
+  const int n = c->ngrids;
+  std::vector<BatchProblem> P(n);
+  std::vector<int> tb(n + 1), cb(n + 1);
+  int tiles = 0, chunks = 0;
+  for (int g = 0; g < n; ++g) {
+    const fv_grid &G = c->grids[g];
+    BatchProblem &p = P[g];
+    memset(&p, 0, sizeof(p));
+    p.off = c->offsets[g];
+    for (int d = 0; d < 2; ++d) {
+      p.n[d] = G.n[d];
+      p.ntile[d] = (G.n[d] + tile[d] - 1) / tile[d];
+      const double h = G.len[d] / G.n[d];
+      p.half_inv_h[d] = 0.5 / h;
+      p.inv_h[d] = G.n[d] / G.len[d];
+    }
+    p.half_inv_h[2] = 0.5;
+    for (int d = 0; d < 3; ++d) {
+      p.bc[d][0] = G.bc[d][0];
+      p.bc[d][1] = G.bc[d][1];
+    }
+    tb[g] = tiles;
+    cb[g] = chunks;
+    tiles += p.ntile[0] * p.ntile[1];
+    chunks += (int)(((long long)G.n[0] * G.n[1] + kBatchChunk - 1) / kBatchChunk);
+  }
+  tb[n] = tiles;
+  cb[n] = chunks;
+  c->b_total_tiles = tiles;
+  c->b_total_chunks = chunks;
+  FV_CK(cudaMemcpy(c->b_prob, P.data(), sizeof(BatchProblem) * n, cudaMemcpyHostToDevice));
+  FV_CK(cudaMemcpy(c->b_tile_begin, tb.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+  FV_CK(cudaMemcpy(c->b_chunk_begin, cb.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+  int per_sm = 0;
+  FV_CK(batch_max_blocks(c->launch.stage[0].threads, batch_smem_bytes(tile), &per_sm));
+  if (per_sm < 1) return FV_EINVAL;
+  c->b_blocks = per_sm * c->sms;
+  return FV_OK;
+}
+
+int batch_init(fv_ctx *c, const fv_grid *grids, int ngrids) {
+  c->ngrids = ngrids;
+  c->grids.assign(grids, grids + ngrids);
+  c->offsets.assign(ngrids + 1, 0);
+  long long off = 0;
+  for (int g = 0; g < ngrids; ++g) {
+    if (grids[g].dim != 2) return FV_EUNSUPPORTED;
+    if (validate_grid(&grids[g])) return FV_EINVAL;
+    c->offsets[g] = off;
+    off += 4ll * grids[g].n[0] * grids[g].n[1];
+    off = (off + 31) / 32 * 32;  // 256-byte aligned blocks
+  }
+  c->offsets[ngrids] = off;
+  c->state_bytes = sizeof(double) * (size_t)off;
+  FV_CK(cudaMalloc(&c->b_prob, sizeof(BatchProblem) * ngrids));
+  FV_CK(cudaMalloc(&c->b_tile_begin, sizeof(int) * (ngrids + 1)));
+  FV_CK(cudaMalloc(&c->b_chunk_begin, sizeof(int) * (ngrids + 1)));
+  FV_CK(cudaMalloc(&c->b_smax, sizeof(unsigned long long) * 2 * ngrids));
+  FV_CK(cudaMalloc(&c->b_tacc, sizeof(double) * ngrids));
+  FV_CK(cudaMalloc(&c->b_bar, sizeof(unsigned) * 2));
+  FV_CK(cudaMemset(c->b_bar, 0, sizeof(unsigned) * 2));
+  return FV_OK;
+}
+
+// nsteps steps of a batch in one cooperative launch, captured in a graph.
+int batch_run(fv_ctx *c, double *Ud, int nsteps, double dt_fixed, bool want_t) {
+  if (nsteps == 0) return FV_OK;
+  const int n = c->ngrids;
+  long long dbits = 0;
+  if (dt_fixed > 0.0) memcpy(&dbits, &dt_fixed, sizeof(dbits));
+  cudaGraphExec_t exec = nullptr;
+  for (auto &g : c->graphs)
+    if (g.U == Ud && g.dt_bits == dbits && g.steps == nsteps) exec = g.exec;
+  if (!exec) {
+    BatchArgs b;
+    memset(&b, 0, sizeof(b));
+    b.prob = c->b_prob;
+    b.tile_begin = c->b_tile_begin;
+    b.chunk_begin = c->b_chunk_begin;
+    b.nprob = n;
+    b.total_tiles = c->b_total_tiles;
+    b.total_chunks = c->b_total_chunks;
+    b.nsteps = nsteps;
+    b.chunk_cells = kBatchChunk;
+    b.tile[0] = c->launch.stage[0].tile[0];
+    b.tile[1] = c->launch.stage[0].tile[1];
+    b.U = Ud;
+    b.U1 = c->U1;
+    b.U2 = c->U2;
+    b.smax = c->b_smax;
+    b.t_acc = c->b_tacc;
+    b.flags = c->flags;
+    b.bar_count = c->b_bar;
+    b.bar_gen = c->b_bar + 1;
+    b.g1 = c->scheme.gamma - 1.0;
+    b.gamma = c->scheme.gamma;
+    b.half_eps = 0.5 * c->scheme.eps;
+    b.efix = c->scheme.efix;
+    b.inv2efix = c->scheme.efix > 0.0 ? 0.5 / c->scheme.efix : 0.0;
+    b.cfl = c->scheme.cfl;
+    b.dt_fixed = dt_fixed > 0.0 ? dt_fixed : 0.0;
+    const int blocks = c->b_blocks < c->b_total_tiles ? c->b_blocks : c->b_total_tiles;
+    cudaGraph_t graph;
+    FV_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(c->b_smax, 0, sizeof(unsigned long long) * 2 * n, c->cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->b_tacc, 0, sizeof(double) * n, c->cap);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->b_bar, 0, sizeof(unsigned), c->cap);
+    if (e == cudaSuccess)
+      e = launch_batch_run(b, blocks, c->launch.stage[0].threads, batch_smem_bytes(b.tile), c->cap);
+    cudaError_t ec = cudaStreamEndCapture(c->cap, &graph);
+    if (e != cudaSuccess) {
+      if (ec == cudaSuccess) cudaGraphDestroy(graph);
+      return cuda_fail(e);
+    }
+    FV_CK(ec);
+    cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    FV_CK(ei);
+    c->graphs.push_back(GraphEntry{Ud, dbits, nsteps, exec});
+  }
+  FV_CK(cudaGraphLaunch(exec, c->stream));
+  (void)want_t;
+  return FV_OK;
+}
+
+}  // namespace
+
+namespace fvk {
+
+int ctx_work_state(fv_ctx *c, const double *U, double **Uw) {
+  int r;
+  if ((r = ensure_staging(c))) return r;
+  FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyDefault, c->stream));
+  FV_CK(cudaStreamSynchronize(c->stream));
+  *Uw = c->stage_in;
+  return FV_OK;
+}
+
+int ctx_time_launch(fv_ctx *c, double *Uw, const fv_launch *l, int steps, int repeats, double *sec) {
+  int r = validate_launch(&c->grid, l, c->smem_optin);
+  if (r) return r;
+  const fv_launch saved = c->launch;
+  c->launch = *l;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<double> t;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = FV_ECUDA;
+  if (!r) r = rk_step_device(c, Uw, 0.0, true, nullptr, c->stream);  // warm-up
+  for (int rep = 0; rep < repeats && !r; ++rep) {
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) r = FV_ECUDA;
+    for (int s = 0; s < steps && !r; ++s) r = rk_step_device(c, Uw, 0.0, true, nullptr, c->stream);
+    float ms = 0.f;
+    if (!r && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+               cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      r = FV_ECUDA;
+    if (!r) t.push_back(1e-3 * ms / steps);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->launch = saved;
+  if (r) {
+    (void)cudaGetLastError();
+    return r;
+  }
+  std::sort(t.begin(), t.end());
+  *sec = t[t.size() / 2];
+  return read_flags(c);
+}
+
+int ctx_sm_count(const fv_ctx *c) { return c->sms; }
+int ctx_validate_launch(const fv_ctx *c, const fv_launch *l) { return validate_launch(&c->grid, l, c->smem_optin); }
+int ctx_default_launch(const fv_ctx *c, fv_launch *l) { return fv_default_launch(&c->grid, l); }
+int ctx_dim(const fv_ctx *c) { return c->grid.dim; }
+
+}  // namespace fvk
+
 extern "C" {
 
 const char *fv_strerror(int status) {
@@ -314,9 +507,8 @@ int fv_default_launch(const fv_grid *g, fv_launch *l) {
 int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, const fv_launch *l, void *stream) {
   if (!out) return FV_EINVAL;
   *out = nullptr;
-  if (ngrids < 1) return FV_EINVAL;
+  if (ngrids < 1 || !grids) return FV_EINVAL;
   if (validate_grid(grids) || validate_scheme(s)) return FV_EINVAL;
-  if (ngrids > 1) return FV_EUNSUPPORTED;
   fv_ctx *c = new (std::nothrow) fv_ctx();
   if (!c) return FV_ENOMEM;
   c->grid = grids[0];
@@ -325,11 +517,13 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
   c->nv = grids[0].dim + 2;
   c->ncells = (long long)grids[0].n[0] * grids[0].n[1] * grids[0].n[2];
   c->state_bytes = sizeof(double) * (size_t)c->nv * (size_t)c->ncells;
+  c->ngrids = 1;
   int r = FV_OK;
   auto fail = [&](int code) {
     fv_destroy(c);
     return code;
   };
+  if (ngrids > 1 && (r = batch_init(c, grids, ngrids))) return fail(r);
   if (cudaGetDevice(&c->device) != cudaSuccess) return fail(cuda_fail(cudaErrorNoDevice));
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return fail(FV_ECUDA);
@@ -353,7 +547,19 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
   c->norm_out = reinterpret_cast<double *>(scr + 32);
   if (cudaMemset(scr, 0, 256) != cudaSuccess) return fail(FV_ECUDA);
   if ((r = set_attributes(c))) return fail(r);
+  if (c->ngrids > 1 && (r = batch_setup(c))) return fail(r);
   *out = c;
+  return FV_OK;
+}
+
+int fv_layout(const fv_ctx *c, long long *offsets, int ngrids) {
+  if (!c || !offsets || ngrids != c->ngrids) return FV_EINVAL;
+  if (c->ngrids == 1) {
+    offsets[0] = 0;
+    offsets[1] = (long long)c->nv * c->ncells;
+    return FV_OK;
+  }
+  for (int g = 0; g <= c->ngrids; ++g) offsets[g] = c->offsets[g];
   return FV_OK;
 }
 
@@ -363,7 +569,9 @@ int fv_set_launch(fv_ctx *c, const fv_launch *l) {
   if (r) return r;
   c->launch = *l;
   drop_graphs(c);
-  return set_attributes(c);
+  if ((r = set_attributes(c))) return r;
+  if (c->ngrids > 1) return batch_setup(c);
+  return FV_OK;
 }
 
 int fv_get_launch(const fv_ctx *c, fv_launch *l) {
@@ -374,6 +582,7 @@ int fv_get_launch(const fv_ctx *c, fv_launch *l) {
 
 int fv_residual(fv_ctx *c, const double *U, double *R, double *rnorm2) {
   if (!c || !U || !R || U == R) return FV_EINVAL;
+  if (c->ngrids > 1) return FV_EUNSUPPORTED;
   int r;
   const bool hostU = !is_device_ptr(U), hostR = !is_device_ptr(R);
   const bool hostN = rnorm2 && !is_device_ptr(rnorm2);
@@ -392,6 +601,12 @@ int fv_residual(fv_ctx *c, const double *U, double *R, double *rnorm2) {
   if (rnorm2) {
     if (c->norm_part_cap < nblk) {
       if (c->norm_part) cudaFree(c->norm_part);
+  if (c->b_prob) cudaFree(c->b_prob);
+  if (c->b_tile_begin) cudaFree(c->b_tile_begin);
+  if (c->b_chunk_begin) cudaFree(c->b_chunk_begin);
+  if (c->b_smax) cudaFree(c->b_smax);
+  if (c->b_tacc) cudaFree(c->b_tacc);
+  if (c->b_bar) cudaFree(c->b_bar);
       c->norm_part = nullptr;
       c->norm_part_cap = 0;
       FV_CK(cudaMalloc(&c->norm_part, sizeof(double) * c->nv * nblk));
@@ -412,6 +627,7 @@ int fv_residual(fv_ctx *c, const double *U, double *R, double *rnorm2) {
 
 int fv_time_step(fv_ctx *c, const double *U, double *dt_out) {
   if (!c || !U || !dt_out) return FV_EINVAL;
+  if (c->ngrids > 1) return FV_EUNSUPPORTED;
   int r;
   const bool hostU = !is_device_ptr(U), hostD = !is_device_ptr(dt_out);
   const double *Ud = U;
@@ -436,6 +652,7 @@ int fv_time_step(fv_ctx *c, const double *U, double *dt_out) {
 
 int fv_rk_step(fv_ctx *c, double *U, double dt, double *dt_used) {
   if (!c || !U) return FV_EINVAL;
+  if (c->ngrids > 1) return fv_run(c, U, 1, dt, dt_used);
   int r;
   const bool hostU = !is_device_ptr(U);
   double *Ud = U;
@@ -465,6 +682,20 @@ int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
     if ((r = ensure_staging(c))) return r;
     FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyHostToDevice, c->stream));
     Ud = c->stage_in;
+  }
+  if (c->ngrids > 1) {
+    if ((r = batch_run(c, Ud, nsteps, dt_fixed, t_out != nullptr))) return r;
+    if (hostU) FV_CK(cudaMemcpyAsync(U, Ud, c->state_bytes, cudaMemcpyDeviceToHost, c->stream));
+    if (t_out) {
+      if (nsteps == 0) {
+        for (int g = 0; g < c->ngrids; ++g) t_out[g] = 0.0;
+      } else {
+        FV_CK(cudaMemcpyAsync(t_out, c->b_tacc, sizeof(double) * c->ngrids, cudaMemcpyDeviceToHost, c->stream));
+      }
+      return read_flags(c);
+    }
+    if (hostU) FV_CK(cudaStreamSynchronize(c->stream));
+    return FV_OK;
   }
   const bool cfl = !(dt_fixed > 0.0);
   long long dbits = 0;
@@ -525,6 +756,12 @@ void fv_destroy(fv_ctx *c) {
   if (c->stage_out) cudaFree(c->stage_out);
   if (c->smax) cudaFree(c->smax);  // start of the scratch block
   if (c->norm_part) cudaFree(c->norm_part);
+  if (c->b_prob) cudaFree(c->b_prob);
+  if (c->b_tile_begin) cudaFree(c->b_tile_begin);
+  if (c->b_chunk_begin) cudaFree(c->b_chunk_begin);
+  if (c->b_smax) cudaFree(c->b_smax);
+  if (c->b_tacc) cudaFree(c->b_tacc);
+  if (c->b_bar) cudaFree(c->b_bar);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }

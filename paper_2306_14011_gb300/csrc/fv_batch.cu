@@ -1,0 +1,224 @@
+// Batched grids: many independent 2D problems of different sizes advanced
+// together by one persistent, cooperative kernel.
+//
+// The kernel runs every step of a call: per step, a time-step phase (each
+// problem's CFL maximum, reduced exactly with atomicMax on bit patterns) and
+// the three SSP-RK3 stage phases.  Within a phase the work items --
+// (problem, cell chunk) or (problem, tile) -- are spread round-robin over all
+// co-resident CTAs; a grid-wide barrier separates the phases.  Each problem
+// keeps its own time step.  Tiles are processed by the same tile_work routine
+// as the single-grid stage kernels (plain loads), so every problem's results
+// are bitwise those of a single-grid run.
+#include "fv_stage.cuh"
+
+namespace fvk {
+
+namespace {
+
+constexpr uint64_t kBarrierWaitNs = 2000000000ull;  // 2 s bound on a grid-barrier wait
+
+// Grid-wide barrier of a cooperative launch: CTA-local barrier, then thread 0
+// arrives on a counter; the last arrival resets it and advances the
+// generation, the others wait for the generation to move (bounded).
+// Returns false in every thread of the CTA if the wait timed out.
+__device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned *flags) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned *vgen = gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const uint64_t t0 = globaltimer_ns();
+      while (*vgen == g) {
+        if (globaltimer_ns() - t0 > kBarrierWaitNs) {
+          atomicOr(flags, FLAG_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Index of the problem whose [begin[p], begin[p+1]) range holds item.
+__device__ __forceinline__ int find_problem(const int *begin, int nprob, int item) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin[mid] <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int MODE>
+__device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double *tile, double *s_coef,
+                                            double (*red)[32]) {
+  const double *Us = MODE == MODE_STAGE1 ? b.U : (MODE == MODE_STAGE2 ? b.U1 : b.U2);
+  double *out = MODE == MODE_STAGE1 ? b.U1 : (MODE == MODE_STAGE2 ? b.U2 : b.U);
+  for (int item = blockIdx.x; item < b.total_tiles; item += gridDim.x) {
+    const int p = find_problem(b.tile_begin, b.nprob, item);
+    const BatchProblem &P = b.prob[p];
+    StageArgs a;
+    a.Us = Us + P.off;
+    a.Un = b.U + P.off;
+    a.out = out + P.off;
+    a.norm_part = nullptr;
+    a.n[0] = P.n[0];
+    a.n[1] = P.n[1];
+    a.n[2] = 1;
+    a.tile[0] = b.tile[0];
+    a.tile[1] = b.tile[1];
+    a.tile[2] = 1;
+    a.ntile[0] = P.ntile[0];
+    a.ntile[1] = P.ntile[1];
+    a.ntile[2] = 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      a.bc[d][0] = P.bc[d][0];
+      a.bc[d][1] = P.bc[d][1];
+      a.half_ds[d] = 0.0;
+      a.half_inv_h[d] = P.half_inv_h[d];
+    }
+    a.use_tma = 0;
+    a.g1 = b.g1;
+    a.half_eps = b.half_eps;
+    a.efix = b.efix;
+    a.inv2efix = b.inv2efix;
+    a.smax = b.dt_fixed > 0.0 ? nullptr : b.smax + (long long)slot * b.nprob + p;
+    a.cfl = b.cfl;
+    a.dt_fixed = b.dt_fixed;
+    a.t_acc = nullptr;
+    a.flags = b.flags;
+    const int local = item - b.tile_begin[p];
+    tile_work<2, MODE>(nullptr, a, local % P.ntile[0], local / P.ntile[0], 0, tile, nullptr, 0u, s_coef, red);
+    __syncthreads();  // the next item reuses the shared buffers
+  }
+  return grid_barrier(b.bar_count, b.bar_gen, b.flags);
+}
+
+// Per problem max over its cells of sum_d (|u_d| + c) / dx_d (as in dt_kernel).
+__device__ __forceinline__ void dt_phase(const BatchArgs &b, int slot) {
+  __shared__ unsigned long long wmax[32];
+  for (int item = blockIdx.x; item < b.total_chunks; item += gridDim.x) {
+    const int p = find_problem(b.chunk_begin, b.nprob, item);
+    const BatchProblem &P = b.prob[p];
+    const long long N = (long long)P.n[0] * P.n[1];
+    const long long c0 = (long long)(item - b.chunk_begin[p]) * b.chunk_cells;
+    const long long c1 = c0 + b.chunk_cells < N ? c0 + b.chunk_cells : N;
+    const double *U = b.U + P.off;
+    unsigned long long best = 0ull;
+    bool bad = false;
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      const double rho = U[c];
+      if (not_positive_finite(rho)) {
+        bad = true;
+        continue;
+      }
+      const double tr = rsqrt_fp64(rho);
+      const double r = tr * tr;
+      const double m0 = U[N + c], m1 = U[2 * N + c];
+      const double u0 = m0 * r, u1 = m1 * r;
+      const double k = fma(m1, u1, m0 * u0);
+      const double pr = b.g1 * fma(-0.5, k, U[3 * N + c]);
+      if (not_positive_finite(pr)) {
+        bad = true;
+        continue;
+      }
+      const double c2 = (b.gamma * pr) * r;
+      const double cs = c2 * rsqrt_fp64(c2);
+      const double s = fma(iabs(u1) + cs, P.inv_h[1], (iabs(u0) + cs) * P.inv_h[0]);
+      const unsigned long long sb = (unsigned long long)dbits(s);
+      best = sb > best ? sb : best;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+      best = o > best ? o : best;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wmax[warp] = best;
+    const int anybad = __syncthreads_or(bad);
+    if (warp == 0) {
+      const int nw = (blockDim.x + 31) >> 5;
+      unsigned long long m = lane < nw ? wmax[lane] : 0ull;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, m, off);
+        m = o > m ? o : m;
+      }
+      if (lane == 0) {
+        atomicMax(b.smax + (long long)slot * b.nprob + p, m);
+        if (anybad) atomicOr(b.flags, FLAG_NONPHYSICAL);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) batch_run_kernel(const BatchArgs b) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ double s_coef[4];
+  __shared__ double red[4][32];
+  double *tile = aligned_smem(smem_raw);
+  for (int step = 0; step < b.nsteps; ++step) {
+    const int slot = step & 1;
+    if (b.dt_fixed <= 0.0) {
+      // clear the other slot for the next step (nobody reads it during this step)
+      if (blockIdx.x == 0)
+        for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) b.smax[(long long)(slot ^ 1) * b.nprob + p] = 0ull;
+      dt_phase(b, slot);
+      if (!grid_barrier(b.bar_count, b.bar_gen, b.flags)) return;
+    }
+    if (blockIdx.x == 0 && b.t_acc)
+      for (int p = threadIdx.x; p < b.nprob; p += blockDim.x)
+        b.t_acc[p] += b.dt_fixed > 0.0 ? b.dt_fixed
+                                       : b.cfl / __longlong_as_double((long long)b.smax[(long long)slot * b.nprob + p]);
+    if (!stage_phase<MODE_STAGE1>(b, slot, tile, s_coef, red)) return;
+    if (!stage_phase<MODE_STAGE2>(b, slot, tile, s_coef, red)) return;
+    if (!stage_phase<MODE_STAGE3>(b, slot, tile, s_coef, red)) return;
+  }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(const int tile[2]) {
+  const int t3[3] = {tile[0], tile[1], 1};
+  return stage_smem_bytes(2, t3);
+}
+
+cudaError_t batch_max_blocks(int threads, size_t smem, int *blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute((const void *)batch_run_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_run_kernel, threads, smem);
+}
+
+cudaError_t launch_batch_run(const BatchArgs &b, int blocks, int threads, size_t smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_run_kernel, b);
+}
+
+}  // namespace fvk

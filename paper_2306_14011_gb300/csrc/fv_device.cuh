@@ -33,14 +33,21 @@ __device__ __forceinline__ double iabs(double x) {
 // a < b for non-negative finite doubles (bit patterns are ordered like the values).
 __device__ __forceinline__ bool ilt_nonneg(double a, double b) { return dbits(a) < dbits(b); }
 
+// Select between two doubles on the integer pipe (a double-typed ?: can be
+// emitted as FP64 moves, which occupy the FP64 pipe).
+__device__ __forceinline__ double isel(bool p, double a, double b) {
+  return __longlong_as_double(p ? dbits(a) : dbits(b));
+}
+
 // minmod(a, b): 0 when the signs differ (or either is zero), else the argument
 // of smaller magnitude.  Bitwise equal to the branchy definition for finite
-// inputs (a zero argument yields a signed zero, which adds as zero).
+// inputs (a zero argument yields a signed zero, which adds as zero).  Integer
+// compares and selects only: no FP64-pipe instruction.
 __device__ __forceinline__ double minmod(double a, double b) {
   const long long ia = dbits(a), ib = dbits(b);
   const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
-  const double m = (ma < mb) ? a : b;
-  return ((ia ^ ib) < 0) ? 0.0 : m;
+  const long long m = (ma < mb) ? ia : ib;
+  return __longlong_as_double(((ia ^ ib) < 0) ? 0ll : m);
 }
 
 // true when x is not a finite positive double (x <= 0, -0, inf or NaN).
@@ -162,8 +169,14 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   double l3 = iabs(un + c);
   const double l2 = iabs(un);
   const double delta = efix * c;
-  if (ilt_nonneg(l1, delta)) l1 = fma(l1, l1, delta * delta) * (tc * inv2efix);
-  if (ilt_nonneg(l3, delta)) l3 = fma(l3, l3, delta * delta) * (tc * inv2efix);
+  const bool fix1 = ilt_nonneg(l1, delta), fix3 = ilt_nonneg(l3, delta);
+  // near sonic points only: a warp-uniform branch keeps the (rare) fix from
+  // being computed unconditionally
+  if (__any_sync(__activemask(), fix1 || fix3)) {
+    const double d2 = delta * delta, s2 = tc * inv2efix;
+    l1 = isel(fix1, fma(l1, l1, d2) * s2, l1);
+    l3 = isel(fix3, fma(l3, l3, d2) * s2, l3);
+  }
 
   // dissipation sum_w |lambda_w| alpha_w r_w
   const double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3;

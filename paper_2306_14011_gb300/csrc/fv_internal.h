@@ -46,6 +46,35 @@ struct DtArgs {
   unsigned *flags;
 };
 
+// One problem of a batched context (2D).
+struct BatchProblem {
+  long long off;         // offset (doubles) of its SoA block in the packed state
+  int n[2];              // cells along x, y
+  int ntile[2];          // tiles along x, y
+  int bc[3][2];          // FV_BC_* per axis side
+  double half_inv_h[3];  // 1 / (2 dx_d)
+  double inv_h[2];       // 1 / dx_d
+};
+
+struct BatchArgs {
+  const BatchProblem *prob;
+  const int *tile_begin;   // [nprob + 1] first tile item of each problem
+  const int *chunk_begin;  // [nprob + 1] first time-step chunk of each problem
+  int nprob, total_tiles, total_chunks, nsteps;
+  long long chunk_cells;
+  int tile[2];
+  double *U, *U1, *U2;           // packed states
+  unsigned long long *smax;      // [2][nprob] bits of each problem's max wave-speed sum
+  double *t_acc;                 // [nprob] simulated time, or null
+  unsigned *flags;
+  unsigned *bar_count, *bar_gen; // grid barrier words
+  double g1, gamma, half_eps, efix, inv2efix, cfl, dt_fixed;
+};
+
+size_t batch_smem_bytes(const int tile[2]);
+cudaError_t batch_max_blocks(int threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_batch_run(const BatchArgs &b, int blocks, int threads, size_t smem, cudaStream_t st);
+
 // Dynamic shared memory of a stage-kernel CTA for a tile shape.
 size_t stage_smem_bytes(int dim, const int tile[3]);
 
@@ -60,4 +89,22 @@ cudaError_t launch_debug_math(const double *x, double *o1, double *o2, long n, c
 // (smem_optin = cudaDeviceProp::sharedMemPerBlockOptin of the current device).
 cudaError_t stage_kernel_attributes(int dim, size_t smem_optin);
 
+}  // namespace fvk
+
+struct fv_ctx;
+struct fv_launch;
+
+namespace fvk {
+// Tuner support (fv_api.cu).  ctx_work_state: copy U (device or host) into the
+// context's staging buffer and return it, so timing runs never touch the
+// caller's state.  ctx_time_launch: with launch l, one warm-up SSP-RK3 step
+// then `steps` timed steps on Uw (CFL dt, direct launches), `repeats` times;
+// *sec = median seconds per step.  Returns FV_EINVAL for an invalid l (nothing
+// launched).  ctx_sm_count: multiprocessors of the context's device.
+int ctx_work_state(fv_ctx *c, const double *U, double **Uw);
+int ctx_time_launch(fv_ctx *c, double *Uw, const fv_launch *l, int steps, int repeats, double *sec);
+int ctx_sm_count(const fv_ctx *c);
+int ctx_validate_launch(const fv_ctx *c, const fv_launch *l);
+int ctx_default_launch(const fv_ctx *c, fv_launch *l);
+int ctx_dim(const fv_ctx *c);
 }  // namespace fvk

@@ -169,21 +169,19 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
   __syncthreads();
 }
 
+// All the work of one tile: stage the tile (TMA with mbarrier `bar` at parity
+// `phase`, or plain loads), compute the face fluxes axis by axis, accumulate
+// the residual and write the epilogue.  `tile` is the CTA's dynamic shared
+// memory (128-byte aligned); s_coef and red are static shared scratch.
+// Returns false (uniformly across the CTA) if the tile load timed out.
 template <int DIM, int MODE>
-__global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
+__device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageArgs &a, int bx, int by, int bz,
+                                          double *tile, uint64_t *mbar, uint32_t phase, double *s_coef,
+                                          double (*red)[32]) {
   constexpr int NV = DIM + 2;
-  extern __shared__ unsigned char smem_raw[];
-  double *tile = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const TileGeom G = tile_geom(DIM, a.tile);
   double *F = tile + NV * G.plane;
   double *R = F + NV * G.fmax;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(R + NV * G.cells);
-
-  int b = blockIdx.x;
-  const int bx = b % a.ntile[0];
-  b /= a.ntile[0];
-  const int by = b % a.ntile[1];
-  const int bz = b / a.ntile[1];
   const int o[3] = {bx * a.tile[0], by * a.tile[1], (DIM == 3) ? bz * a.tile[2] : 0};
   int ext[3];
   ext[0] = min(a.tile[0], a.n[0] - o[0]);
@@ -195,24 +193,19 @@ __global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ CUte
   if (a.use_tma) {
     const uint32_t bar = smem_u32(mbar);
     if (threadIdx.x == 0) {
-      mbar_init(bar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
       mbar_expect_tx(bar, (uint32_t)(NV * G.plane * sizeof(double)));
       if (DIM == 2)
-        tma_load_3d(smem_u32(tile), &tmap, o[0] - 2, o[1] - 2, 0, bar);
+        tma_load_3d(smem_u32(tile), tmap, o[0] - 2, o[1] - 2, 0, bar);
       else
-        tma_load_4d(smem_u32(tile), &tmap, o[0] - 2, o[1] - 2, o[2] - 2, 0, bar);
+        tma_load_4d(smem_u32(tile), tmap, o[0] - 2, o[1] - 2, o[2] - 2, 0, bar);
     }
-    const bool ok = mbar_wait_bounded(bar, 0, kTmaWaitNs);
+    const bool ok = mbar_wait_bounded(bar, phase, kTmaWaitNs);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicOr(a.flags, FLAG_TIMEOUT);
-        mbar_wait_bounded(bar, 0, kTmaWaitNs);  // let a late copy land before the CTA exits
+        mbar_wait_bounded(bar, phase, kTmaWaitNs);  // let a late copy land before the CTA moves on
       }
-      return;
+      return false;
     }
     load_halo<DIM>(tile, a, o, ext, G, true);
   } else {
@@ -229,22 +222,25 @@ __global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ CUte
     }
     load_halo<DIM>(tile, a, o, ext, G, false);
   }
-  __syncthreads();
 
-  // ---- 2./3. face fluxes and their differences per axis
-  double dt = 0.0, w = 0.0;
-  if (MODE != MODE_RESIDUAL) {
-    dt = a.smax ? a.cfl / __longlong_as_double((long long)*a.smax) : a.dt_fixed;
-    w = (MODE == MODE_STAGE1) ? 1.0 : ((MODE == MODE_STAGE2) ? 0.25 : 2.0 / 3.0);
+  // ---- 2./3. face fluxes and their differences per axis.  The step and the
+  // per-axis scales are formed once per CTA (an FP64 division per thread
+  // would cost ~2% of the kernel's FP64 work).
+  if (threadIdx.x == 0) {
+    double dt = 0.0, w = 0.0;
+    if (MODE != MODE_RESIDUAL) {
+      dt = a.smax ? a.cfl / __longlong_as_double((long long)*a.smax) : a.dt_fixed;
+      w = (MODE == MODE_STAGE1) ? 1.0 : ((MODE == MODE_STAGE2) ? 0.25 : 2.0 / 3.0);
+    }
+    s_coef[0] = dt;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) s_coef[1 + d] = (MODE == MODE_RESIDUAL) ? a.half_ds[d] : -w * dt * a.half_inv_h[d];
   }
-  const double cx = (MODE == MODE_RESIDUAL) ? a.half_ds[0] : -w * dt * a.half_inv_h[0];
-  const double cy = (MODE == MODE_RESIDUAL) ? a.half_ds[1] : -w * dt * a.half_inv_h[1];
-  face_pass<DIM, 0>(tile, F, R, a, ext, G, cx);
-  face_pass<DIM, 1>(tile, F, R, a, ext, G, cy);
-  if constexpr (DIM == 3) {
-    const double cz = (MODE == MODE_RESIDUAL) ? a.half_ds[2] : -w * dt * a.half_inv_h[2];
-    face_pass<DIM, 2>(tile, F, R, a, ext, G, cz);
-  }
+  __syncthreads();
+  const double dt = s_coef[0];
+  face_pass<DIM, 0>(tile, F, R, a, ext, G, s_coef[1]);
+  face_pass<DIM, 1>(tile, F, R, a, ext, G, s_coef[2]);
+  if constexpr (DIM == 3) face_pass<DIM, 2>(tile, F, R, a, ext, G, s_coef[3]);
 
   // ---- 4. epilogue
   const int ncell = ext[0] * ext[1] * ext[2];
@@ -276,27 +272,71 @@ __global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ CUte
       a.out[v * N + gi] = outv;
     }
   }
-  if (MODE == MODE_STAGE3 && a.t_acc && blockIdx.x == 0 && threadIdx.x == 0) *a.t_acc += dt;
+  if (MODE == MODE_STAGE3 && a.t_acc && bx == 0 && by == 0 && bz == 0 && threadIdx.x == 0) *a.t_acc += dt;
 
   if (want_norm) {
     // CTA partial sums of R_v^2 (fixed reduction order: lanes, then warps)
-    __shared__ double red[NV][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double s = nrm[v];
+      double sum = nrm[v];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-      if (lane == 0) red[v][warp] = s;
+      for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+      if (lane == 0) red[v][warp] = sum;
     }
     __syncthreads();
     if (threadIdx.x < NV) {
-      double s = 0.0;
+      double sum = 0.0;
       const int nw = (blockDim.x + 31) >> 5;
-      for (int q = 0; q < nw; ++q) s += red[threadIdx.x][q];
-      a.norm_part[(long long)blockIdx.x * NV + threadIdx.x] = s;
+      for (int q = 0; q < nw; ++q) sum += red[threadIdx.x][q];
+      const long long tix = ((long long)bz * a.ntile[1] + by) * a.ntile[0] + bx;
+      a.norm_part[tix * NV + threadIdx.x] = sum;
     }
   }
+  return true;
+}
+
+// Dynamic shared memory of the stage kernels: tile box, face buffer, residual
+// accumulator, then one mbarrier.
+template <int DIM>
+__device__ __forceinline__ uint64_t *stage_mbar(double *tile, const StageArgs &a) {
+  constexpr int NV = DIM + 2;
+  const TileGeom G = tile_geom(DIM, a.tile);
+  return reinterpret_cast<uint64_t *>(tile + NV * (G.plane + G.fmax + G.cells));
+}
+
+__device__ __forceinline__ double *aligned_smem(unsigned char *raw) {
+  return reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+}
+
+// One CTA per tile of the grid.  Register budget: FV_STAGE_MIN_BLOCKS resident
+// 256-thread CTAs per SM (4 by default: 64 registers per thread; the default
+// 2D tile's shared memory also allows four).  More warps per SM hide the phase
+// barriers; the FP64 instruction count does not depend on the budget.
+#ifndef FV_STAGE_MIN_BLOCKS
+#define FV_STAGE_MIN_BLOCKS 4
+#endif
+template <int DIM, int MODE>
+__global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
+  constexpr int NV = DIM + 2;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ double s_coef[4];
+  __shared__ double red[NV][32];
+  double *tile = aligned_smem(smem_raw);
+  uint64_t *mbar = stage_mbar<DIM>(tile, a);
+  if (a.use_tma) {
+    if (threadIdx.x == 0) {
+      mbar_init(smem_u32(mbar), 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  int b = blockIdx.x;
+  const int bx = b % a.ntile[0];
+  b /= a.ntile[0];
+  const int by = b % a.ntile[1];
+  const int bz = b / a.ntile[1];
+  tile_work<DIM, MODE>(&tmap, a, bx, by, bz, tile, mbar, 0u, s_coef, red);
 }
 
 template <int DIM>

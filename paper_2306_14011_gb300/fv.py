@@ -49,6 +49,27 @@ class fv_launch(C.Structure):
     _fields_ = [("stage", fv_kernel_cfg * 3), ("dt", fv_kernel_cfg)]
 
 
+class fv_mlp_hyper(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("lr", C.c_double),
+                ("eps", C.c_double), ("tol", C.c_double), ("batch", C.c_int), ("max_epochs", C.c_int),
+                ("n_iter_no_change", C.c_int)]
+
+
+class fv_tune_opts(C.Structure):
+    _fields_ = [("samples", C.c_int), ("steps", C.c_int), ("repeats", C.c_int), ("candidates", C.c_int),
+                ("top", C.c_int), ("exhaustive", C.c_int), ("final_repeats", C.c_int), ("rounds", C.c_int),
+                ("refine", C.c_int), ("seed", C.c_ulonglong),
+                ("hidden", C.c_int * 4), ("mlp", fv_mlp_hyper)]
+
+
+class fv_tune_report(C.Structure):
+    _fields_ = [("t_default", C.c_double), ("t_tuned", C.c_double), ("t_best_sampled", C.c_double),
+                ("t_exhaustive", C.c_double), ("r2_train", C.c_double), ("r2_test", C.c_double),
+                ("space_size", C.c_double), ("n_params", C.c_int), ("n_train", C.c_int), ("n_test", C.c_int),
+                ("epochs", C.c_int), ("n_measured", C.c_int), ("n_exhaustive", C.c_int), ("rounds", C.c_int),
+                ("n_refined", C.c_int), ("exhaustive_best", fv_launch)]
+
+
 _lib = None
 _VP = C.c_void_p
 
@@ -76,6 +97,15 @@ def load() -> C.CDLL:
         L.fv_debug_math.argtypes = [_VP, _VP, _VP, C.c_long, _VP]
         L.fv_residual_noalloc.argtypes = [P(fv_grid), P(fv_scheme), _VP, _VP, _VP, _VP]
         L.fv_residual_noalloc.restype = C.c_int
+        L.fv_mlp_train.argtypes = [C.c_int, P(C.c_int), _VP, _VP, _VP, C.c_long, _VP, C.c_int, P(fv_mlp_hyper),
+                                   P(C.c_double), P(C.c_int), _VP]
+        L.fv_mlp_train.restype = C.c_int
+        L.fv_mlp_predict.argtypes = [C.c_int, P(C.c_int), _VP, _VP, C.c_long, _VP, _VP]
+        L.fv_mlp_predict.restype = C.c_int
+        L.fv_tune.argtypes = [_VP, _VP, P(fv_tune_opts), P(fv_launch), P(fv_tune_report)]
+        L.fv_tune.restype = C.c_int
+        L.fv_layout.argtypes = [_VP, P(C.c_longlong), C.c_int]
+        L.fv_layout.restype = C.c_int
         for name in ("fv_default_launch", "fv_init", "fv_set_launch", "fv_get_launch", "fv_residual",
                      "fv_time_step", "fv_rk_step", "fv_run", "fv_sync", "fv_debug_math"):
             getattr(L, name).restype = C.c_int
@@ -165,11 +195,20 @@ def fv_default_launch(g) -> fv_launch:
 
 
 def fv_init(g, scheme: fv_scheme, launch: Optional[fv_launch] = None, stream=None) -> int:
+    """g: a GridSpec, or a list of 2D GridSpecs for a batched context."""
     ctx = _VP()
-    G = make_grid(g)
-    _check(load().fv_init(C.byref(ctx), C.byref(G), 1, C.byref(scheme), C.byref(launch) if launch else None,
+    grids = list(g) if isinstance(g, (list, tuple)) else [g]
+    G = (fv_grid * len(grids))(*[make_grid(x) for x in grids])
+    _check(load().fv_init(C.byref(ctx), G, len(grids), C.byref(scheme), C.byref(launch) if launch else None,
                           _stream_handle(stream)), "fv_init")
     return ctx.value
+
+
+def fv_layout(ctx: int, ngrids: int):
+    """Offsets (in doubles) of each grid's block in the packed state, plus the total."""
+    off = (C.c_longlong * (ngrids + 1))()
+    _check(load().fv_layout(ctx, off, ngrids), "fv_layout")
+    return [off[i] for i in range(ngrids + 1)]
 
 
 def fv_set_launch(ctx: int, launch: fv_launch):
@@ -201,11 +240,14 @@ def fv_rk_step(ctx: int, U, dt: float = 0.0, want_dt: bool = False) -> Optional[
     return d.value if want_dt else None
 
 
-def fv_run(ctx: int, U, nsteps: int, dt_fixed: float = 0.0, want_time: bool = False) -> Optional[float]:
-    t = C.c_double()
+def fv_run(ctx: int, U, nsteps: int, dt_fixed: float = 0.0, want_time: bool = False, ngrids: int = 1):
+    """Returns the simulated time (a list of ngrids times for a batch) if want_time."""
+    t = (C.c_double * ngrids)()
     _check(load().fv_run(ctx, _ptr(U), int(nsteps), float(dt_fixed), C.addressof(t) if want_time else None),
            "fv_run")
-    return t.value if want_time else None
+    if not want_time:
+        return None
+    return t[0] if ngrids == 1 else [t[i] for i in range(ngrids)]
 
 
 def fv_sync(ctx: int):
@@ -227,6 +269,57 @@ def fv_residual_noalloc(g, scheme: fv_scheme, U, R, rnorm2=None, stream=None):
            "fv_residual_noalloc")
 
 
+def mlp_hyper(**kw) -> fv_mlp_hyper:
+    """Table "para-setting" values unless overridden."""
+    d = dict(alpha=1e-4, beta1=0.95, beta2=0.90, lr=9e-4, eps=1e-9, tol=1e-6, batch=200, max_epochs=200,
+             n_iter_no_change=10)
+    d.update(kw)
+    return fv_mlp_hyper(**d)
+
+
+def fv_mlp_train(sizes, params, X, y, order, hyper: fv_mlp_hyper, stream=None):
+    """Train on the device in place.  sizes: layer widths; params, X, y, order:
+    CUDA tensors (float64 params/X/y, int32 order [epochs][n]).  Returns the
+    list of per-epoch mean losses actually run."""
+    nl = len(sizes) - 1
+    S = (C.c_int * len(sizes))(*sizes)
+    epochs = order.shape[0]
+    losses = (C.c_double * max(1, epochs))()
+    ran = C.c_int()
+    _check(load().fv_mlp_train(nl, S, _ptr(params), _ptr(X), _ptr(y), X.shape[0], order.data_ptr(), epochs,
+                               C.byref(hyper), losses, C.byref(ran), _stream_handle(stream)), "fv_mlp_train")
+    return [losses[i] for i in range(ran.value)]
+
+
+def fv_mlp_predict(sizes, params, X, out, stream=None):
+    nl = len(sizes) - 1
+    S = (C.c_int * len(sizes))(*sizes)
+    _check(load().fv_mlp_predict(nl, S, _ptr(params), _ptr(X), X.shape[0], _ptr(out), _stream_handle(stream)),
+           "fv_mlp_predict")
+
+
+def fv_tune(ctx: int, U, **opts):
+    """Autotune the context's launch configuration for state U (not modified).
+    opts: fields of fv_tune_opts (samples, steps, repeats, candidates, top,
+    exhaustive, final_repeats, seed, hidden=(...)).  Returns (launch dict,
+    report dict); the tuned launch is installed in the context."""
+    o = fv_tune_opts()
+    for k, v in opts.items():
+        if k == "hidden":
+            for i, w in enumerate(v):
+                o.hidden[i] = w
+        elif k == "mlp":
+            o.mlp = v
+        else:
+            setattr(o, k, v)
+    best = fv_launch()
+    rep = fv_tune_report()
+    _check(load().fv_tune(ctx, _ptr(U), C.byref(o), C.byref(best), C.byref(rep)), "fv_tune")
+    report = {f[0]: getattr(rep, f[0]) for f in fv_tune_report._fields_ if f[0] != "exhaustive_best"}
+    report["exhaustive_best"] = launch_to_dict(rep.exhaustive_best) if rep.n_exhaustive else None
+    return launch_to_dict(best), report
+
+
 def fv_debug_math(x, out_rsqrt, out_rcp, stream=None):
     _check(load().fv_debug_math(_ptr(x), _ptr(out_rsqrt), _ptr(out_rcp), x.numel(), _stream_handle(stream)),
            "fv_debug_math")
@@ -242,16 +335,38 @@ class Solver:
     """
 
     def __init__(self, grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, launch=None, stream=None):
-        self.grid = grid
+        self.batched = isinstance(grid, (list, tuple))
+        self.grids = list(grid) if self.batched else [grid]
+        self.grid = self.grids[0]
+        self.ngrids = len(self.grids)
         self.scheme = make_scheme(gamma, cfl, eps, kappa, efix)
         if isinstance(launch, dict):
             launch = launch_from_dict(launch)
         self.ctx = fv_init(grid, self.scheme, launch, stream)
+        self.offsets = fv_layout(self.ctx, self.ngrids)
 
     # shapes
     def _chk(self, U):
-        if tuple(U.shape) != tuple(self.grid.shape):
-            raise ValueError(f"state shape {tuple(U.shape)} != grid shape {tuple(self.grid.shape)}")
+        shape = (self.offsets[-1],) if self.batched else tuple(self.grid.shape)
+        if tuple(U.shape) != shape:
+            raise ValueError(f"state shape {tuple(U.shape)} != expected {shape}")
+
+    def pack(self, states, out=None):
+        """Packed state of a batch from one array per grid (numpy or torch)."""
+        import torch
+        first = states[0]
+        if out is None:
+            out = (np.zeros(self.offsets[-1]) if isinstance(first, np.ndarray)
+                   else torch.zeros(self.offsets[-1], dtype=torch.float64, device=first.device))
+        for g, (S, gs) in enumerate(zip(states, self.grids)):
+            out[self.offsets[g]:self.offsets[g] + S.numel() if not isinstance(S, np.ndarray) else
+                self.offsets[g] + S.size] = S.reshape(-1)
+        return out
+
+    def unpack(self, U):
+        """Views of each grid's state in a packed batch."""
+        return [U[self.offsets[g]:self.offsets[g] + int(np.prod(gs.shape))].reshape(gs.shape)
+                for g, gs in enumerate(self.grids)]
 
     @property
     def launch(self) -> dict:
@@ -282,7 +397,12 @@ class Solver:
 
     def run(self, U, nsteps: int, dt_fixed: float = 0.0, return_time: bool = False):
         self._chk(U)
-        return fv_run(self.ctx, U, nsteps, dt_fixed, want_time=return_time)
+        return fv_run(self.ctx, U, nsteps, dt_fixed, want_time=return_time, ngrids=self.ngrids)
+
+    def tune(self, U, **opts):
+        """Run the autotuner on state U; installs and returns the tuned launch."""
+        self._chk(U)
+        return fv_tune(self.ctx, U, **opts)
 
     def sync(self):
         fv_sync(self.ctx)
