@@ -37,13 +37,15 @@ N_CELLS_SIDE = 4096
 METRIC = "FP64 cell-updates/s per RK stage (2D Euler KH 4096^2, MUSCL-minmod + Roe + SSP-RK3)"
 UNIT = "cell-stage/s"
 # Algorithmic FP64 work per cell and RK stage, counted on the CPU oracle with an
-# operation-counting scalar (python -m oracle.count_flops; 2D value at n = 4096):
-# every +, -, *, /, sqrt of the plain method counts one FLOP.
+# operation-counting scalar (python -m oracle.count_flops; 2D value at n = 4096,
+# 3D at n = 384): every +, -, *, /, sqrt of the plain method counts one FLOP.
 FLOP_PER_CELL_STAGE_2D = 496.44
-# Algorithmic HBM bytes per cell-stage: stage 1 reads U^n and writes U^1 (4+4
-# doubles), stages 2 and 3 read U^s and U^n and write (12 doubles): 256 B per
-# cell and step over 3 stages.
+FLOP_PER_CELL_STAGE_3D = 959.62
+# Algorithmic HBM bytes per cell-stage: stage 1 reads U^n and writes U^1 (nvar
+# + nvar doubles), stages 2 and 3 read U^s and U^n and write (3 nvar doubles):
+# 8 nvar doubles per cell and step over 3 stages.
 BYTES_PER_CELL_STAGE_2D = 256.0 / 3.0
+BYTES_PER_CELL_STAGE_3D = 320.0 / 3.0
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz
 # (a DFMA loop measured 1.18 TFLOP/s on this part).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -145,12 +147,15 @@ def run_ours(args):
 
     dist, rank, world = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
-    n = args.n
-    g, U0 = I.kelvin_helmholtz(n, seed=1)
-    cells = g.ncells
     stream = torch.cuda.current_stream()
+    W = make_workload(args, I)
+    g, U0 = W["grid"], W["U0"]
+    cells = W["cells"]
     solver = fv.Solver(g, stream=stream)
-    U = torch.from_numpy(U0).to(dev)
+    U = torch.from_numpy(U0).to(dev) if not W["batched"] else solver.pack(
+        [torch.from_numpy(u).to(dev) for u in W["states"]])
+    if W["batched"]:
+        U0 = U.cpu().numpy()
 
     def barrier():
         if dist is not None:
@@ -176,20 +181,24 @@ def run_ours(args):
     ms_max = t_dev.item()
     solver.sync()  # reports non-physical / timeout flags of the timed region
 
-    # dominant kernel (fused stage kernel): average launch duration over the
-    # timed region = (timed region - K x the time-step reduction) / (3 K); the
-    # reduction (memset + dt kernel) is timed alone with CUDA events right after.
-    dtbuf = torch.zeros(1, dtype=torch.float64, device=dev)
-    reps = max(3, min(args.steps, 20))
-    fv.fv_time_step(solver.ctx, U, dtbuf)
-    torch.cuda.synchronize()
-    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    for _ in range(reps):
+    # dominant kernel.  Single grid (fused stage kernel): average launch
+    # duration over the timed region = (timed region - K x the time-step
+    # reduction) / (3 K); the reduction (memset + dt kernel) is timed alone with
+    # CUDA events right after.  Batch: the one persistent launch of the timed
+    # region, per RK stage (it also runs the per-problem CFL phases).
+    dt_ms = 0.0
+    if not W["batched"]:
+        dtbuf = torch.zeros(1, dtype=torch.float64, device=dev)
+        reps = max(3, min(args.steps, 20))
         fv.fv_time_step(solver.ctx, U, dtbuf)
-    e3.record(stream)
-    torch.cuda.synchronize()
-    dt_ms = e2.elapsed_time(e3) / reps
+        torch.cuda.synchronize()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(reps):
+            fv.fv_time_step(solver.ctx, U, dtbuf)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        dt_ms = e2.elapsed_time(e3) / reps
     stage_ms = (ms - args.steps * dt_ms) / (3 * args.steps)
 
     # end to end through the C ABI with a pinned host state
@@ -215,11 +224,11 @@ def run_ours(args):
         return None
 
     value = world * cells * 3 * args.steps / (ms_max / 1e3)
-    flops_per_launch = FLOP_PER_CELL_STAGE_2D * cells
+    flops_per_launch = W["flop"] * cells
     achieved_tflops = flops_per_launch / (stage_ms / 1e3) / 1e12
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
-    achieved_gbs = BYTES_PER_CELL_STAGE_2D * cells / (stage_ms / 1e3) / 1e9
+    achieved_gbs = W["bytes"] * cells / (stage_ms / 1e3) / 1e9
     traffic = STAGE_TRAFFIC["bytes"] if STAGE_TRAFFIC["source_hash"] == kernel_source_hash() else None
     line = {
         "metric": METRIC,
@@ -234,29 +243,116 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded Kelvin-Helmholtz initial condition)",
-        "config": {"workload": f"2D Euler Kelvin-Helmholtz {n}x{n} periodic, FP64, MUSCL-minmod + Roe + SSP-RK3, "
-                               f"CFL 0.5; 1 bench step = 1 SSP-RK3 step (dt reduction + 3 fused stage kernels) "
-                               f"replayed from a CUDA graph",
-                   "cells": cells, "launch": "default", "launch_params": solver.launch,
+        "config": {"workload": W["desc"], "cells": cells, "launch": "default", "launch_params": solver.launch,
                    "l2": "state (%.0f MB) larger than L2, no flush" % (U0.nbytes / 1e6),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "fvk::stage_kernel<2, stage>", "stage_ms": stage_ms, "dt_kernel_ms": dt_ms,
-                     "flop_per_cell_stage": FLOP_PER_CELL_STAGE_2D,
+                     "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic if W["name"] == "kh4096" else None,
+                     "kernel": W["kernel"], "stage_ms": stage_ms, "dt_kernel_ms": dt_ms,
+                     "flop_per_cell_stage": W["flop"],
                      "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz",
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                      "hbm_frac": (achieved_gbs / hbm_peak) if hbm_peak else None,
-                     "bytes_per_cell_stage": BYTES_PER_CELL_STAGE_2D},
+                     "bytes_per_cell_stage": W["bytes"]},
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": W["launches_per_step"] * args.steps if not W["batched"] else 1,
         "clocks": clk,
         "impl": "ours",
     }
+    if args.workload != "kh4096":
+        line["metric"] = W["metric"]
+    if args.tune and not W["batched"]:
+        best, rep = solver.tune(U, samples=args.tune_samples, steps=3, candidates=200000, top=16, rounds=3, refine=2,
+                                exhaustive=1, final_repeats=7, seed=7)
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        solver.run(U, args.warmup)
+        torch.cuda.synchronize()
+        e4.record(stream)
+        solver.run(U, args.steps)
+        e5.record(stream)
+        torch.cuda.synchronize()
+        tuned_value = cells * 3 * args.steps / (e4.elapsed_time(e5) / 1e3)
+        line["tuned"] = {"value": tuned_value, "speedup_vs_default": tuned_value / value, "launch": best,
+                         "tuner": {k: v for k, v in rep.items() if k != "exhaustive_best"},
+                         "exhaustive_best": rep["exhaustive_best"]}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args, U0, g)
+        line["cpu_baseline"] = W["cpu_baseline"]()
     solver.close()
     return line
+
+
+def make_workload(args, I):
+    """The benchmark workloads: the metric's KH 4096^2 (default), the 3D
+    Taylor-Green 384^3 and the batched rotated-Sod set (96 grids)."""
+    if args.workload == "kh4096":
+        n = args.n
+        g, U0 = I.kelvin_helmholtz(n, seed=1)
+        return dict(name="kh4096", grid=g, U0=U0, cells=g.ncells, batched=False, flop=FLOP_PER_CELL_STAGE_2D,
+                    bytes=BYTES_PER_CELL_STAGE_2D, kernel="fvk::stage_kernel<2, stage>", launches_per_step=4,
+                    metric=METRIC,
+                    desc=f"2D Euler Kelvin-Helmholtz {n}x{n} periodic, FP64, MUSCL-minmod + Roe + SSP-RK3, CFL 0.5; "
+                         f"1 bench step = 1 SSP-RK3 step (dt reduction + 3 fused stage kernels) replayed from a "
+                         f"CUDA graph",
+                    cpu_baseline=lambda: cpu_baseline(args, U0, g))
+    if args.workload == "tgv384":
+        n = 384 if args.n == N_CELLS_SIDE else args.n
+        g, U0 = I.taylor_green(n, seed=2)
+        return dict(name="tgv384", grid=g, U0=U0, cells=g.ncells, batched=False, flop=FLOP_PER_CELL_STAGE_3D,
+                    bytes=BYTES_PER_CELL_STAGE_3D, kernel="fvk::stage_kernel<3, stage>", launches_per_step=4,
+                    metric=f"FP64 cell-updates/s per RK stage (3D Euler Taylor-Green {n}^3)",
+                    desc=f"3D Euler Taylor-Green {n}^3 periodic, M=0.1, 1e-4 pressure noise, FP64, MUSCL-minmod + "
+                         f"Roe + SSP-RK3, CFL 0.5; 1 bench step = 1 SSP-RK3 step replayed from a CUDA graph",
+                    cpu_baseline=lambda: cpu_baseline_3d(args, U0, g))
+    specs = I.batched_sod(96, seed=3)
+    probs = [I.sod_rotated(nn, th) for nn, th in specs]
+    grids = [p[0] for p in probs]
+    cells = sum(gg.ncells for gg in grids)
+    return dict(name="sod96", grid=grids, U0=None, states=[p[1] for p in probs], cells=cells, batched=True,
+                flop=FLOP_PER_CELL_STAGE_2D, bytes=BYTES_PER_CELL_STAGE_2D,
+                kernel="fvk::batch_run_kernel (persistent, all steps)", launches_per_step=1,
+                metric="FP64 cell-updates/s per RK stage (96 batched 2D Sod grids, 64^2..2048^2)",
+                desc=f"96 rotated 2D Sod problems, sizes log-uniform in [64, 2048] (seed 3), {cells} cells, "
+                     f"transmissive, FP64, per-problem CFL 0.5; all bench steps in one persistent cooperative "
+                     f"launch under a CUDA graph",
+                cpu_baseline=lambda: cpu_baseline_batch(args, probs))
+
+
+def cpu_baseline_3d(args, U0, g):
+    """The oracle on a z-slab of the 3D state (periodic in x, y; transmissive at
+    the slab's z faces), ~10 s of CPU work."""
+    from oracle import oracle as O
+    from paper_2306_14011_gb300 import inputs as I
+    nz = 32
+    gb = I.GridSpec(3, (g.n[0], g.n[1], nz), (g.length[0], g.length[1], g.length[2] * nz / g.n[2]),
+                    ((0, 0), (0, 0), (1, 1)))
+    Ub = np.ascontiguousarray(U0[:, :nz])
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        Ub, _ = O.run(gb, Ub, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= args.cpu_seconds or steps >= 20:
+            break
+    return {"value": gb.ncells * 3 * steps / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 step(s) of the C++ oracle on a {g.n[0]}x{g.n[1]}x{nz} slab ({el:.1f} s)"}
+
+
+def cpu_baseline_batch(args, probs):
+    """The oracle stepping the batch's problems one after another (smallest
+    first) for ~10 s."""
+    from oracle import oracle as O
+    order = sorted(range(len(probs)), key=lambda i: probs[i][0].ncells)
+    cells, t0, done = 0, time.perf_counter(), 0
+    for i in order:
+        g, U = probs[i]
+        O.run(g, U, 1)
+        cells += g.ncells
+        done += 1
+        if time.perf_counter() - t0 >= args.cpu_seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": cells * 3 / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"one SSP-RK3 step of the {done} smallest problems with the C++ oracle ({el:.1f} s)"}
 
 
 def _band(U0, g, rows):
@@ -326,11 +422,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=N_CELLS_SIDE, help="grid cells per side (default: the workload's 4096)")
+    ap.add_argument("--workload", choices=("kh4096", "tgv384", "sod96"), default="kh4096",
+                    help="kh4096: the metric's configuration (default); tgv384: 3D Taylor-Green; "
+                         "sod96: 96 batched Sod grids")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--ref-rows", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="also run the autotuner and time its launch")
+    ap.add_argument("--tune-samples", type=int, default=300)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     line = run_reference(args) if args.impl == "reference" else run_ours(args)

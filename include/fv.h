@@ -153,6 +153,22 @@ int fv_rk_step(fv_ctx *ctx, double *U, double dt, double *dt_used);
  * waits longer than 2 s ends the kernel with FV_ETIMEOUT. */
 int fv_run(fv_ctx *ctx, double *U, int nsteps, double dt_fixed, double *t_out);
 
+/* Discrete adjoint (vector-Jacobian products), FP64, single-grid contexts.
+ * what = FV_VJP_RESIDUAL: out = (dR_h/dU)^T lambda, R_h of Eq. (5) with face
+ *   areas as fv_residual returns it (dt ignored).
+ * what = FV_VJP_RKSTEP: out = (dU^{n+1}/dU^n)^T lambda for one SSP-RK3 step
+ *   of fv_rk_step with the step held fixed at dt > 0 (the CFL step's
+ *   dependence on U is not differentiated).
+ * U (the state the Jacobian is taken at), lambda and out: caller-owned device
+ * arrays of nvar*ncells doubles; out must not alias U or lambda.
+ * Non-differentiable points follow the forward-mode convention: |x|' =
+ * sign(x) with sign(+0) = +1; the entropy fix and the limiter take the branch
+ * the forward pass took; minmod(a, b) passes the derivative of the argument it
+ * returns (b on ties) and none when a and b do not share one strict sign.
+ * Stream-ordered; allocates two adjoint work states on first use. */
+enum { FV_VJP_RESIDUAL = 0, FV_VJP_RKSTEP = 1 };
+int fv_adjoint_vjp(fv_ctx *ctx, int what, const double *U, const double *lambda, double dt, double *out);
+
 /* Wait for all work of the context and report (then clear) device-side
  * flags: FV_ENONPHYSICAL, FV_ETIMEOUT, or FV_OK. */
 int fv_sync(fv_ctx *ctx);

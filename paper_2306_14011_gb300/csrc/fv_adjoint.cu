@@ -1,0 +1,277 @@
+// Discrete adjoint of the residual: out = sum_d scale_d J_d(U)^T lam, with J_d
+// the Jacobian of the axis-d flux differences, plus a linear combination of up
+// to three arrays (the reverse of the SSP-RK3 stage combinations).
+//
+// lam^T R = sum over faces f of ds (lam_{f-1} - lam_f) . F_f, F_f the flux
+// between cells f-1 and f from the MUSCL states of cells f-2..f+1.  One CTA
+// per tile computes, for every face whose stencil touches the tile, the
+// cotangents of its left/right states (roe_2F_vjp) and pushes them through the
+// reconstruction to the four stencil cells; each cell then gathers what its
+// faces sent it, so no atomics are needed.  Halos: 3 cells of U, 2 of lam.
+// With transmissive boundaries the faces outside [0, n] do not exist and the
+// boundary cells also collect what was sent to their ghost copies.
+#include "../../include/fv.h"
+#include "fv_adjoint.cuh"
+#include "fv_stage.cuh"
+
+namespace fvk {
+
+namespace {
+
+struct AdjGeom {
+  int UX, UY, UZ, uplane;  // U box with halo 3
+  int LX, LY, LZ, lplane;  // lam box with halo 2
+  int fmax, cells;
+};
+
+__host__ __device__ inline AdjGeom adj_geom(int dim, const int tile[3]) {
+  AdjGeom g;
+  const int tx = tile[0], ty = tile[1], tz = dim == 3 ? tile[2] : 1;
+  g.UX = tx + 6;
+  g.UY = ty + 6;
+  g.UZ = dim == 3 ? tz + 6 : 1;
+  g.uplane = g.UX * g.UY * g.UZ;
+  g.LX = tx + 4;
+  g.LY = ty + 4;
+  g.LZ = dim == 3 ? tz + 4 : 1;
+  g.lplane = g.LX * g.LY * g.LZ;
+  const int fx = (tx + 3) * ty * tz, fy = tx * (ty + 3) * tz, fz = dim == 3 ? tx * ty * (tz + 3) : 0;
+  g.fmax = fx > fy ? fx : fy;
+  g.fmax = g.fmax > fz ? g.fmax : fz;
+  g.cells = tx * ty * tz;
+  return g;
+}
+
+// Box of `halo` cells around the valid tile, every variable, plain loads with
+// the boundary index map (corners included; they are never read).  With
+// zero_transmissive, cells beyond a transmissive side are 0 instead: they are
+// ghosts, which carry no residual and hence no cotangent.
+template <int DIM>
+__device__ void load_box(double *dst, const double *src, const AdjArgs &a, const int o[3], const int ext[3],
+                         int halo, int BX, int BY, int plane, bool zero_transmissive) {
+  constexpr int NV = DIM + 2;
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+  const int ex = ext[0] + 2 * halo, ey = ext[1] + 2 * halo, ez = DIM == 3 ? ext[2] + 2 * halo : 1;
+  const int cnt = ex * ey * ez;
+  for (int c = threadIdx.x; c < cnt; c += blockDim.x) {
+    const int i = c % ex, r = c / ex, j = r % ey, k = r / ey;
+    const int cx = o[0] - halo + i, cy = o[1] - halo + j, cz = DIM == 3 ? o[2] - halo + k : 0;
+    bool ghost_zero = false;
+    if (zero_transmissive) {
+      const int cc[3] = {cx, cy, cz};
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+        ghost_zero = ghost_zero || (cc[d] < 0 && a.bc[d][0] == FV_BC_TRANSMISSIVE) ||
+                     (cc[d] >= a.n[d] && a.bc[d][1] == FV_BC_TRANSMISSIVE);
+    }
+    const int gx = ghost_source(cx, a.n[0], a.bc[0][0], a.bc[0][1]);
+    const int gy = ghost_source(cy, a.n[1], a.bc[1][0], a.bc[1][1]);
+    const int gz = DIM == 3 ? ghost_source(cz, a.n[2], a.bc[2][0], a.bc[2][1]) : 0;
+    const long long s = ((long long)gz * a.n[1] + gy) * a.n[0] + gx;
+    const int d = (k * BY + j) * BX + i;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * plane + d] = ghost_zero ? 0.0 : src[v * N + s];
+  }
+}
+
+// Faces along axis D: per face the cotangents sent to its four stencil cells
+// (c0..c3 for cells f-2 .. f+1), stored as 4*NV doubles; then every tile cell
+// gathers and accumulates scale * (sum) into acc.
+template <int DIM, int D>
+__device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb, double *acc, const AdjArgs &a,
+                              const int o[3], const int ext[3], const AdjGeom &G, double scale) {
+  constexpr int NV = DIM + 2;
+  constexpr int NT = DIM - 1;
+  constexpr int E = NV - 1;
+  const int fe0 = ext[0] + (D == 0 ? 3 : 0), fe1 = ext[1] + (D == 1 ? 3 : 0);
+  const int fe2 = DIM == 3 ? ext[2] + (D == 2 ? 3 : 0) : 1;
+  const int nf = fe0 * fe1 * fe2;
+  const int us = D == 0 ? 1 : (D == 1 ? G.UX : G.UX * G.UY);  // U stencil stride
+  const int ls = D == 0 ? 1 : (D == 1 ? G.LX : G.LX * G.LY);  // lam stride
+  const double h = a.half_eps;
+  const bool lo_trans = a.bc[D][0] == FV_BC_TRANSMISSIVE, hi_trans = a.bc[D][1] == FV_BC_TRANSMISSIVE;
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    const int i = f % fe0, rr = f / fe0, j = rr % fe1, k = rr / fe1;
+    // face index along D (global): between cells fg-1 and fg
+    const int loc[3] = {i, j, k};
+    const int fg = o[D] - 1 + loc[D];
+    double *out = Fb + f;  // 4*NV values at stride G.fmax
+    const bool real = !((lo_trans && fg < 0) || (hi_trans && fg > a.n[D]));
+    if (!real) {
+#pragma unroll
+      for (int q = 0; q < 4 * NV; ++q) out[q * G.fmax] = 0.0;
+      continue;
+    }
+    // U stencil: cells fg-2 .. fg+1 -> U box coordinate along D: (fg-2) - (o[D]-3) = loc[D]
+    const int ux = D == 0 ? i : i + 3, uy = D == 1 ? j : j + 3, uz = DIM == 3 ? (D == 2 ? k : k + 3) : 0;
+    const double *pu = Ubox + (uz * G.UY + uy) * G.UX + ux;
+    // lam at cells fg-1 and fg -> lam box coordinate along D: (fg-1) - (o[D]-2) = loc[D]
+    const int lx = D == 0 ? i : i + 2, ly = D == 1 ? j : j + 2, lz = DIM == 3 ? (D == 2 ? k : k + 2) : 0;
+    const double *pl = Lbox + (lz * G.LY + ly) * G.LX + lx;
+    double QL[NV], QR[NV], gb[NV];
+    int pL[NV], pR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double *q = pu + v * G.uplane;
+      const double q0 = q[0], q1 = q[us], q2 = q[2 * us], q3 = q[3 * us];
+      const double dm = q1 - q0, d0 = q2 - q1, dp = q3 - q2;
+      QL[v] = fma(h, minmod(dm, d0), q1);
+      QR[v] = fma(-h, minmod(d0, dp), q2);
+      pL[v] = minmod_pick(dm, d0);
+      pR[v] = minmod_pick(d0, dp);
+      gb[v] = pl[v * G.lplane] - pl[v * G.lplane + ls];
+    }
+    double qL[NT + 3], qR[NT + 3], Gb[NT + 3], bL[NT + 3], bR[NT + 3];
+    qL[0] = QL[0];
+    qR[0] = QR[0];
+    Gb[0] = gb[0];
+    qL[1] = QL[1 + D];
+    qR[1] = QR[1 + D];
+    Gb[1] = gb[1 + D];
+    int t = 0;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      if (ax == D) continue;
+      qL[2 + t] = QL[1 + ax];
+      qR[2 + t] = QR[1 + ax];
+      Gb[2 + t] = gb[1 + ax];
+      ++t;
+    }
+    qL[E] = QL[E];
+    qR[E] = QR[E];
+    Gb[E] = gb[E];
+    roe_2F_vjp<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gb, bL, bR);
+    double QLb[NV], QRb[NV];
+    QLb[0] = bL[0];
+    QRb[0] = bR[0];
+    QLb[1 + D] = bL[1];
+    QRb[1 + D] = bR[1];
+    t = 0;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      if (ax == D) continue;
+      QLb[1 + ax] = bL[2 + t];
+      QRb[1 + ax] = bR[2 + t];
+      ++t;
+    }
+    QLb[E] = bL[E];
+    QRb[E] = bR[E];
+    // through the reconstruction: QL = q1 + h mm(q1-q0, q2-q1), QR = q2 - h mm(q2-q1, q3-q2)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double hl = h * QLb[v], hr = h * QRb[v];
+      const double c0 = pL[v] == 1 ? -hl : 0.0;
+      const double c1 = QLb[v] + (pL[v] == 1 ? hl : (pL[v] == 2 ? -hl : 0.0)) + (pR[v] == 1 ? hr : 0.0);
+      const double c2 = QRb[v] - (pR[v] == 1 ? hr : (pR[v] == 2 ? -hr : 0.0)) + (pL[v] == 2 ? hl : 0.0);
+      const double c3 = pR[v] == 2 ? -hr : 0.0;
+      out[(4 * v + 0) * G.fmax] = c0;
+      out[(4 * v + 1) * G.fmax] = c1;
+      out[(4 * v + 2) * G.fmax] = c2;
+      out[(4 * v + 3) * G.fmax] = c3;
+    }
+  }
+  __syncthreads();
+  // gather: cell c (local index m along D) receives c0 of face m+2, c1 of m+1,
+  // c2 of m, c3 of m-1 (local face index = global face - (o[D]-1)); boundary
+  // cells of transmissive sides also collect what was sent to their ghosts.
+  const int ncell = ext[0] * ext[1] * (DIM == 3 ? ext[2] : 1);
+  const int fstride = D == 0 ? 1 : (D == 1 ? fe0 : fe0 * fe1);
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = c % ext[0], rr = c / ext[0], j = rr % ext[1], k = rr / ext[1];
+    const int loc[3] = {i, j, k};
+    const int m = loc[D];
+    // face (m + 1) in local face coordinates sits at face index f0 below
+    int fi[3] = {i, j, k};
+    fi[D] = m + 1;  // local index of face between cells m-1 and m, i.e. global face o[D]+m
+    const int fc = (fi[2] * fe1 + fi[1]) * fe0 + fi[0];  // face "m" (global o[D]+m)
+    const int gcell = o[D] + m;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double *P = Fb + (4 * v) * G.fmax;
+      double s = P[0 * G.fmax + fc + 2 * fstride]   // c0 of face m+2
+                 + P[1 * G.fmax + fc + fstride]     // c1 of face m+1
+                 + P[2 * G.fmax + fc]               // c2 of face m
+                 + P[3 * G.fmax + fc - fstride];    // c3 of face m-1
+      if (lo_trans && gcell == 0) {
+        // ghosts -2, -1 are copies of cell 0: face 0 sends c0 (cell -2) and c1
+        // (cell -1), face 1 sends c0 (cell -1)
+        s += P[0 * G.fmax + fc] + P[1 * G.fmax + fc] + P[0 * G.fmax + fc + fstride];
+      }
+      if (hi_trans && gcell == a.n[D] - 1) {
+        // ghosts n, n+1 are copies of cell n-1: face n sends c2 (cell n) and c3
+        // (cell n+1), face n-1 sends c3 (cell n)
+        s += P[2 * G.fmax + fc + fstride] + P[3 * G.fmax + fc + fstride] + P[3 * G.fmax + fc];
+      }
+      if (D == 0)
+        acc[v * G.cells + c] = scale * s;
+      else
+        acc[v * G.cells + c] = fma(scale, s, acc[v * G.cells + c]);
+    }
+  }
+  __syncthreads();
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256, 2) adjoint_kernel(const AdjArgs a) {
+  constexpr int NV = DIM + 2;
+  extern __shared__ unsigned char smem_raw[];
+  double *Ubox = aligned_smem(smem_raw);
+  const AdjGeom G = adj_geom(DIM, a.tile);
+  double *Lbox = Ubox + NV * G.uplane;
+  double *Fb = Lbox + NV * G.lplane;
+  double *acc = Fb + 4 * NV * G.fmax;
+  int b = blockIdx.x;
+  const int bx = b % a.ntile[0];
+  b /= a.ntile[0];
+  const int by = b % a.ntile[1];
+  const int bz = b / a.ntile[1];
+  const int o[3] = {bx * a.tile[0], by * a.tile[1], DIM == 3 ? bz * a.tile[2] : 0};
+  int ext[3];
+  ext[0] = min(a.tile[0], a.n[0] - o[0]);
+  ext[1] = min(a.tile[1], a.n[1] - o[1]);
+  ext[2] = DIM == 3 ? min(a.tile[2], a.n[2] - o[2]) : 1;
+  load_box<DIM>(Ubox, a.U, a, o, ext, 3, G.UX, G.UY, G.uplane, false);
+  load_box<DIM>(Lbox, a.lam, a, o, ext, 2, G.LX, G.LY, G.lplane, true);
+  __syncthreads();
+  adj_face_pass<DIM, 0>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[0]);
+  adj_face_pass<DIM, 1>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[1]);
+  if constexpr (DIM == 3) adj_face_pass<DIM, 2>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[2]);
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+  const int ncell = ext[0] * ext[1] * ext[2];
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = c % ext[0], rr = c / ext[0], j = rr % ext[1], k = rr / ext[1];
+    const long long gi = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double r = acc[v * G.cells + c];
+      if (a.A) r = fma(a.cA, a.A[v * N + gi], r);
+      if (a.B) r = fma(a.cB, a.B[v * N + gi], r);
+      if (a.C) r = fma(a.cC, a.C[v * N + gi], r);
+      a.out[v * N + gi] = r;
+    }
+  }
+}
+
+}  // namespace
+
+size_t adjoint_smem_bytes(int dim, const int tile[3]) {
+  const AdjGeom G = adj_geom(dim, tile);
+  const int nv = dim + 2;
+  return 128 + sizeof(double) * (size_t)nv * (G.uplane + G.lplane + 4 * G.fmax + G.cells);
+}
+
+cudaError_t launch_adjoint(int dim, const AdjArgs &a, int threads, cudaStream_t st) {
+  const size_t smem = adjoint_smem_bytes(dim, a.tile);
+  const unsigned blocks = (unsigned)((long long)a.ntile[0] * a.ntile[1] * a.ntile[2]);
+  cudaError_t e;
+  if (dim == 2) {
+    e = cudaFuncSetAttribute((const void *)adjoint_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) adjoint_kernel<2><<<blocks, threads, smem, st>>>(a);
+  } else {
+    e = cudaFuncSetAttribute((const void *)adjoint_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) adjoint_kernel<3><<<blocks, threads, smem, st>>>(a);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+}  // namespace fvk

@@ -87,6 +87,7 @@ struct fv_ctx {
   double *norm_out;           // scratch: nvar norms
   double *norm_part;          // scratch: per-CTA partials (lazy)
   long long norm_part_cap;
+  double *X1, *X2;            // adjoint work states (lazy)
   std::vector<GraphEntry> graphs;
   // batched contexts (ngrids > 1)
   int ngrids;
@@ -283,6 +284,23 @@ void drop_graphs(fv_ctx *c) {
   c->graphs.clear();
 }
 
+// Graphs are keyed by the state pointer; callers that allocate a new state
+// per call would grow the cache without bound, so keep the newest entries.
+constexpr size_t kMaxGraphs = 16;
+void remember_graph(fv_ctx *c, const GraphEntry &e) {
+  // evict the oldest entries of other states (the caller may hold a sibling
+  // graph of e.U that it is about to launch)
+  for (size_t i = 0; c->graphs.size() >= kMaxGraphs && i < c->graphs.size();) {
+    if (c->graphs[i].U != e.U) {
+      cudaGraphExecDestroy(c->graphs[i].exec);
+      c->graphs.erase(c->graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+  c->graphs.push_back(e);
+}
+
 }  // namespace
 
 namespace {
@@ -410,7 +428,7 @@ int batch_run(fv_ctx *c, double *Ud, int nsteps, double dt_fixed, bool want_t) {
     cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     FV_CK(ei);
-    c->graphs.push_back(GraphEntry{Ud, dbits, nsteps, exec});
+    remember_graph(c, GraphEntry{Ud, dbits, nsteps, exec});
   }
   FV_CK(cudaGraphLaunch(exec, c->stream));
   (void)want_t;
@@ -601,6 +619,8 @@ int fv_residual(fv_ctx *c, const double *U, double *R, double *rnorm2) {
   if (rnorm2) {
     if (c->norm_part_cap < nblk) {
       if (c->norm_part) cudaFree(c->norm_part);
+  if (c->X1) cudaFree(c->X1);
+  if (c->X2) cudaFree(c->X2);
   if (c->b_prob) cudaFree(c->b_prob);
   if (c->b_tile_begin) cudaFree(c->b_tile_begin);
   if (c->b_chunk_begin) cudaFree(c->b_chunk_begin);
@@ -724,7 +744,7 @@ int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
     cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     FV_CK(ei);
-    c->graphs.push_back(GraphEntry{Ud, dbits, steps, exec});
+    remember_graph(c, GraphEntry{Ud, dbits, steps, exec});
     (pass == 0 ? gK : g1) = exec;
   }
   for (int left = nsteps; left > 0;) {
@@ -739,6 +759,74 @@ int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
   }
   if (hostU) FV_CK(cudaStreamSynchronize(c->stream));
   return FV_OK;
+}
+
+namespace {
+
+// One adjoint launch over the whole grid.
+int adjoint(fv_ctx *c, const double *U, const double *lam, double *out, double w_dt, const double *A, double cA,
+            const double *B, double cB, const double *Cc, double cC) {
+  const fv_grid &g = c->grid;
+  AdjArgs a;
+  memset(&a, 0, sizeof(a));
+  a.U = U;
+  a.lam = lam;
+  a.out = out;
+  a.A = A;
+  a.B = B;
+  a.C = Cc;
+  a.cA = cA;
+  a.cB = cB;
+  a.cC = cC;
+  const int tile2[3] = {16, 16, 1}, tile3[3] = {8, 4, 4};
+  const int *tile = g.dim == 2 ? tile2 : tile3;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = g.n[d];
+    a.tile[d] = tile[d];
+    a.ntile[d] = (d < g.dim) ? (g.n[d] + tile[d] - 1) / tile[d] : 1;
+    a.bc[d][0] = g.bc[d][0];
+    a.bc[d][1] = g.bc[d][1];
+  }
+  double h[3];
+  for (int d = 0; d < 3; ++d) h[d] = (d < g.dim) ? g.len[d] / g.n[d] : 1.0;
+  for (int d = 0; d < 3; ++d) {
+    if (w_dt == 0.0) {  // residual: face area / 2 (the flux routine's output is 2F)
+      double ds = 1.0;
+      for (int e = 0; e < g.dim; ++e)
+        if (e != d) ds *= h[e];
+      a.scale[d] = 0.5 * ds;
+    } else {  // RK stage: -w dt / (2 dx_d), the transposed stage update
+      a.scale[d] = -w_dt * 0.5 / h[d];
+    }
+  }
+  a.g1 = c->scheme.gamma - 1.0;
+  a.half_eps = 0.5 * c->scheme.eps;
+  a.efix = c->scheme.efix;
+  a.inv2efix = c->scheme.efix > 0.0 ? 0.5 / c->scheme.efix : 0.0;
+  FV_CK(launch_adjoint(g.dim, a, 256, c->stream));
+  return FV_OK;
+}
+
+}  // namespace
+
+extern "C" int fv_adjoint_vjp(fv_ctx *c, int what, const double *U, const double *lam, double dt, double *out) {
+  if (!c || !U || !lam || !out || out == U || out == lam) return FV_EINVAL;
+  if (c->ngrids > 1) return FV_EUNSUPPORTED;
+  if (!is_device_ptr(U) || !is_device_ptr(lam) || !is_device_ptr(out)) return FV_EINVAL;
+  if (what == FV_VJP_RESIDUAL) return adjoint(c, U, lam, out, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0);
+  if (what != FV_VJP_RKSTEP || !(dt > 0.0)) return FV_EINVAL;
+  if (!c->X1) FV_CK(cudaMalloc(&c->X1, c->state_bytes));
+  if (!c->X2) FV_CK(cudaMalloc(&c->X2, c->state_bytes));
+  int r;
+  // forward stage states of the step: U1 = U + dt L(U), U2 = 3/4 U + 1/4 (U1 + dt L(U1))
+  if ((r = stage(c, MODE_STAGE1, 0, U, U, c->U1, nullptr, dt, nullptr, nullptr, c->stream))) return r;
+  if ((r = stage(c, MODE_STAGE2, 1, c->U1, U, c->U2, nullptr, dt, nullptr, nullptr, c->stream))) return r;
+  // reverse: X2 = dJ/dU2 = 2/3 lam + 2/3 dt (dL/dU2)^T lam
+  if ((r = adjoint(c, c->U2, lam, c->X2, (2.0 / 3.0) * dt, lam, 2.0 / 3.0, nullptr, 0.0, nullptr, 0.0))) return r;
+  // X1 = dJ/dU1 = 1/4 X2 + 1/4 dt (dL/dU1)^T X2
+  if ((r = adjoint(c, c->U1, c->X2, c->X1, 0.25 * dt, c->X2, 0.25, nullptr, 0.0, nullptr, 0.0))) return r;
+  // out = 1/3 lam + 3/4 X2 + X1 + dt (dL/dU)^T X1
+  return adjoint(c, U, c->X1, out, dt, lam, 1.0 / 3.0, c->X2, 0.75, c->X1, 1.0);
 }
 
 int fv_sync(fv_ctx *c) {
@@ -756,6 +844,8 @@ void fv_destroy(fv_ctx *c) {
   if (c->stage_out) cudaFree(c->stage_out);
   if (c->smax) cudaFree(c->smax);  // start of the scratch block
   if (c->norm_part) cudaFree(c->norm_part);
+  if (c->X1) cudaFree(c->X1);
+  if (c->X2) cudaFree(c->X2);
   if (c->b_prob) cudaFree(c->b_prob);
   if (c->b_tile_begin) cudaFree(c->b_tile_begin);
   if (c->b_chunk_begin) cudaFree(c->b_chunk_begin);

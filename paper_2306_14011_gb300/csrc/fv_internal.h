@@ -71,6 +71,20 @@ struct BatchArgs {
   double g1, gamma, half_eps, efix, inv2efix, cfl, dt_fixed;
 };
 
+// Adjoint (vector-Jacobian product) kernel: out = sum_d scale_d J_d(U)^T lam
+// + cA A + cB B + cC C (A, B, C may be null).
+struct AdjArgs {
+  const double *U, *lam;
+  double *out;
+  const double *A, *B, *C;
+  double cA, cB, cC;
+  double scale[3];
+  int n[3], tile[3], ntile[3], bc[3][2];
+  double g1, half_eps, efix, inv2efix;
+};
+size_t adjoint_smem_bytes(int dim, const int tile[3]);
+cudaError_t launch_adjoint(int dim, const AdjArgs &a, int threads, cudaStream_t st);
+
 size_t batch_smem_bytes(const int tile[2]);
 cudaError_t batch_max_blocks(int threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_batch_run(const BatchArgs &b, int blocks, int threads, size_t smem, cudaStream_t st);

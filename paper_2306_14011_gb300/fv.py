@@ -106,6 +106,8 @@ def load() -> C.CDLL:
         L.fv_tune.restype = C.c_int
         L.fv_layout.argtypes = [_VP, P(C.c_longlong), C.c_int]
         L.fv_layout.restype = C.c_int
+        L.fv_adjoint_vjp.argtypes = [_VP, C.c_int, _VP, _VP, C.c_double, _VP]
+        L.fv_adjoint_vjp.restype = C.c_int
         for name in ("fv_default_launch", "fv_init", "fv_set_launch", "fv_get_launch", "fv_residual",
                      "fv_time_step", "fv_rk_step", "fv_run", "fv_sync", "fv_debug_math"):
             getattr(L, name).restype = C.c_int
@@ -320,9 +322,22 @@ def fv_tune(ctx: int, U, **opts):
     return launch_to_dict(best), report
 
 
+FV_VJP_RESIDUAL, FV_VJP_RKSTEP = 0, 1
+
+
+def fv_adjoint_vjp(ctx: int, what: int, U, lam, dt: float, out):
+    """out = (dR/dU)^T lam (what = FV_VJP_RESIDUAL) or (dU_{n+1}/dU_n)^T lam for
+    one SSP-RK3 step with fixed dt (FV_VJP_RKSTEP).  Device tensors."""
+    _check(load().fv_adjoint_vjp(ctx, what, _ptr(U), _ptr(lam), float(dt), _ptr(out)), "fv_adjoint_vjp")
+
+
 def fv_debug_math(x, out_rsqrt, out_rcp, stream=None):
     _check(load().fv_debug_math(_ptr(x), _ptr(out_rsqrt), _ptr(out_rcp), x.numel(), _stream_handle(stream)),
            "fv_debug_math")
+
+
+def torch_empty_like(U):
+    return U.new_empty(U.shape)
 
 
 # ----------------------------------------------------------------------------- convenience wrapper
@@ -398,6 +413,18 @@ class Solver:
     def run(self, U, nsteps: int, dt_fixed: float = 0.0, return_time: bool = False):
         self._chk(U)
         return fv_run(self.ctx, U, nsteps, dt_fixed, want_time=return_time, ngrids=self.ngrids)
+
+    def residual_vjp(self, U, lam, out=None):
+        """(dR/dU)^T lam."""
+        out = torch_empty_like(U) if out is None else out
+        fv_adjoint_vjp(self.ctx, FV_VJP_RESIDUAL, U, lam, 0.0, out)
+        return out
+
+    def rk_step_vjp(self, U, lam, dt: float, out=None):
+        """(dU_{n+1}/dU_n)^T lam for one fixed-dt SSP-RK3 step taken from U."""
+        out = torch_empty_like(U) if out is None else out
+        fv_adjoint_vjp(self.ctx, FV_VJP_RKSTEP, U, lam, dt, out)
+        return out
 
     def tune(self, U, **opts):
         """Run the autotuner on state U; installs and returns the tuned launch."""

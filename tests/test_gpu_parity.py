@@ -346,3 +346,21 @@ def test_contexts_with_different_tile_shapes_coexist():
     finally:
         big.close()
         small.close()
+
+
+def test_graph_cache_eviction_keeps_results_identical():
+    """fv_run caches graphs per state pointer (at most 16); runs on many
+    distinct buffers must all reproduce the same trajectory."""
+    g, U = I.isentropic_vortex(64, seed=2)
+    with fv.Solver(g) as s:
+        ref = dev(U)
+        s.run(ref, 20)
+        keep = []
+        for _ in range(24):
+            X = dev(U)
+            keep.append(X)  # distinct live pointers: 48 graphs requested
+            s.run(X, 20)
+            assert torch.equal(X, ref)
+        s.run(keep[0], 20)  # an evicted pointer is captured again
+        s.run(ref, 20)
+        assert torch.equal(keep[0], ref)
