@@ -61,14 +61,21 @@ typedef struct fv_grid {
   int bc[3][2];
 } fv_grid;
 
+enum { FV_LIM_MINMOD = 0, FV_LIM_VANLEER = 1, FV_LIM_NONE = 2 };
+
 /* gamma: ratio of specific heats (1.4).  cfl: CFL number (0.5).
- * eps, kappa: MUSCL parameters of Eq. (6); eps = 1 gives second order; with
- * the minmod limiter the two kappa-weighted limited slopes are equal, so
- * kappa has no effect on the result (accepted for completeness).
+ * eps, kappa: MUSCL parameters of Eq. (6); eps = 1 gives second order.
+ * limiter: the Psi of Eq. (6) -- FV_LIM_MINMOD (Psi(r) = max(0, min(1, r)),
+ * the default), FV_LIM_VANLEER (Psi(r) = (r + |r|)/(1 + |r|)) or FV_LIM_NONE
+ * (Psi = 1: the unlimited kappa-scheme, kappa = -1 upwind, 0 Fromm, 1/3 third
+ * order, 1 central).  With either limiter the two kappa-weighted limited
+ * slopes are equal, so kappa matters only for FV_LIM_NONE.  Batched contexts
+ * and the adjoint support FV_LIM_MINMOD only.
  * efix: Harten entropy-fix width as a fraction of the Roe sound speed (0.1);
  * 0 disables the fix. */
 typedef struct fv_scheme {
   double gamma, cfl, eps, kappa, efix;
+  int limiter;
 } fv_scheme;
 
 enum { FV_LOADER_TMA = 0, FV_LOADER_PLAIN = 1 };

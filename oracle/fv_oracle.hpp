@@ -37,12 +37,15 @@ struct Grid {
   int bc[3][2];      // per axis, (low, high) side
 };
 
+enum { LIM_MINMOD = 0, LIM_VANLEER = 1, LIM_NONE = 2 };
+
 struct Scheme {
   double gamma;  // ratio of specific heats (1.4)
   double cfl;    // CFL number of the time-step rule (0.5)
   double eps;    // MUSCL eps of Eq. (6): 1 -> second order
   double kappa;  // MUSCL kappa of Eq. (6): -1 -> fully upwind
   double efix;   // Harten entropy-fix width as a fraction of the Roe sound speed
+  int limiter;   // Psi of Eq. (6): LIM_MINMOD, LIM_VANLEER or LIM_NONE (Psi = 1)
 };
 
 // ---------------------------------------------------------------- scalar helpers
@@ -60,12 +63,26 @@ T minmod(const T &a, const T &b) {
   return T(0.0);
 }
 
-// Psi^{+}_{k-1/2} times (Q_k - Q_{k-1}) and Psi^{-}_{k+1/2} times (Q_{k+1} - Q_k).
-// With the minmod limiter Psi(r) = max(0, min(1, r)) and r the ratio of the
-// neighbouring difference to this one, Psi(r) * d equals minmod(d, d_neighbour)
-// exactly; this division-free form avoids 0/0 when a difference vanishes.
+// van Leer's limiter in limited-difference form: Psi(r) = (r + |r|) / (1 + |r|)
+// with r = d_neighbour / d gives Psi(r) d = 2 d d_neighbour / (d + d_neighbour)
+// when d and d_neighbour have one strict sign, else 0.
 template <class T>
-T limited(const T &d, const T &d_neighbour) { return minmod(d, d_neighbour); }
+T vanleer(const T &a, const T &b) {
+  if ((value(a) > 0.0 && value(b) > 0.0) || (value(a) < 0.0 && value(b) < 0.0)) return 2.0 * a * b / (a + b);
+  return T(0.0);
+}
+
+// Psi^{+}_{k-1/2} times (Q_k - Q_{k-1}) and Psi^{-}_{k+1/2} times (Q_{k+1} - Q_k):
+// Psi evaluated at r, the ratio of the neighbouring difference to this one,
+// times this difference.  For minmod, Psi(r) = max(0, min(1, r)), the product
+// equals minmod(d, d_neighbour) exactly; this division-free form avoids 0/0
+// when a difference vanishes.  Without a limiter, Psi = 1.
+template <class T>
+T limited(int lim, const T &d, const T &d_neighbour) {
+  if (lim == LIM_VANLEER) return vanleer(d, d_neighbour);
+  if (lim == LIM_NONE) return d;
+  return minmod(d, d_neighbour);
+}
 
 // MUSCL extrapolation, Eq. (6), for one scalar component on the stencil
 // q0 = Q_{k-1}, q1 = Q_k, q2 = Q_{k+1}, q3 = Q_{k+2}; returns Q^L_{k+1/2} and
@@ -75,10 +92,10 @@ void muscl(const Scheme &s, const T &q0, const T &q1, const T &q2, const T &q3, 
   T dm = q1 - q0;  // Q_k - Q_{k-1}
   T d0 = q2 - q1;  // Q_{k+1} - Q_k
   T dp = q3 - q2;  // Q_{k+2} - Q_{k+1}
-  T psi_p_km = limited(dm, d0);  // Psi^+_{k-1/2} (Q_k - Q_{k-1})
-  T psi_m_kp = limited(d0, dm);  // Psi^-_{k+1/2} (Q_{k+1} - Q_k)
-  T psi_p_kp = limited(d0, dp);  // Psi^+_{k+1/2} (Q_{k+1} - Q_k)
-  T psi_m_k3 = limited(dp, d0);  // Psi^-_{k+3/2} (Q_{k+2} - Q_{k+1})
+  T psi_p_km = limited(s.limiter, dm, d0);  // Psi^+_{k-1/2} (Q_k - Q_{k-1})
+  T psi_m_kp = limited(s.limiter, d0, dm);  // Psi^-_{k+1/2} (Q_{k+1} - Q_k)
+  T psi_p_kp = limited(s.limiter, d0, dp);  // Psi^+_{k+1/2} (Q_{k+1} - Q_k)
+  T psi_m_k3 = limited(s.limiter, dp, d0);  // Psi^-_{k+3/2} (Q_{k+2} - Q_{k+1})
   // Eq. (6); a term whose weight (1 -+ kappa) is zero is left out (with
   // kappa = -1 the two (1 + kappa) terms vanish), which changes no result.
   const double e4 = s.eps / 4.0, wm = 1.0 - s.kappa, wp = 1.0 + s.kappa;

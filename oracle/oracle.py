@@ -20,13 +20,16 @@ class Grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("len", C.c_double * 3), ("bc", (C.c_int * 2) * 3)]
 
 
+LIM_MINMOD, LIM_VANLEER, LIM_NONE = 0, 1, 2
+
+
 class Scheme(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("eps", C.c_double), ("kappa", C.c_double),
-                ("efix", C.c_double)]
+                ("efix", C.c_double), ("limiter", C.c_int)]
 
 
-def scheme(gamma=GAMMA, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1) -> Scheme:
-    return Scheme(gamma, cfl, eps, kappa, efix)
+def scheme(gamma=GAMMA, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, limiter=LIM_MINMOD) -> Scheme:
+    return Scheme(gamma, cfl, eps, kappa, efix, limiter)
 
 
 _lib = None

@@ -128,6 +128,7 @@ int validate_grid(const fv_grid *g) {
 int validate_scheme(const fv_scheme *s) {
   if (!s || !(s->gamma > 1.0) || !(s->cfl > 0.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0))
     return FV_EINVAL;
+  if (s->limiter != FV_LIM_MINMOD && s->limiter != FV_LIM_VANLEER && s->limiter != FV_LIM_NONE) return FV_EINVAL;
   return FV_OK;
 }
 
@@ -209,6 +210,9 @@ int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, dou
     a.half_ds[d] = 0.5 * ds;  // halved: the flux routine returns 2F
     a.half_inv_h[d] = 0.5 / h[d];
   }
+  a.limiter = c->scheme.limiter;
+  a.cL = 0.25 * c->scheme.eps * (1.0 - c->scheme.kappa);
+  a.cR = 0.25 * c->scheme.eps * (1.0 + c->scheme.kappa);
   a.g1 = c->scheme.gamma - 1.0;
   a.half_eps = 0.5 * c->scheme.eps;
   a.efix = c->scheme.efix;
@@ -541,6 +545,7 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
     fv_destroy(c);
     return code;
   };
+  if (ngrids > 1 && s->limiter != FV_LIM_MINMOD) return fail(FV_EUNSUPPORTED);
   if (ngrids > 1 && (r = batch_init(c, grids, ngrids))) return fail(r);
   if (cudaGetDevice(&c->device) != cudaSuccess) return fail(cuda_fail(cudaErrorNoDevice));
   cudaDeviceProp prop;
@@ -811,7 +816,7 @@ int adjoint(fv_ctx *c, const double *U, const double *lam, double *out, double w
 
 extern "C" int fv_adjoint_vjp(fv_ctx *c, int what, const double *U, const double *lam, double dt, double *out) {
   if (!c || !U || !lam || !out || out == U || out == lam) return FV_EINVAL;
-  if (c->ngrids > 1) return FV_EUNSUPPORTED;
+  if (c->ngrids > 1 || c->scheme.limiter != FV_LIM_MINMOD) return FV_EUNSUPPORTED;
   if (!is_device_ptr(U) || !is_device_ptr(lam) || !is_device_ptr(out)) return FV_EINVAL;
   if (what == FV_VJP_RESIDUAL) return adjoint(c, U, lam, out, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0);
   if (what != FV_VJP_RKSTEP || !(dt > 0.0)) return FV_EINVAL;

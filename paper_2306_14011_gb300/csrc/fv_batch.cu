@@ -93,6 +93,8 @@ __device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double
       a.half_inv_h[d] = P.half_inv_h[d];
     }
     a.use_tma = 0;
+    a.limiter = FV_LIM_MINMOD;
+    a.cL = a.cR = 0.0;
     a.g1 = b.g1;
     a.half_eps = b.half_eps;
     a.efix = b.efix;

@@ -90,6 +90,15 @@ __device__ __forceinline__ double rcp_fp64(double x) {
   return fma(y, ee, y);
 }
 
+// van Leer's limited slope, 2ab / (a + b) when a and b share one strict sign,
+// else 0 (sign tests and the select on the integer pipe; 7 FP64 operations).
+__device__ __forceinline__ double vanleer(double a, double b) {
+  const long long ia = dbits(a), ib = dbits(b);
+  const bool ok = ((ia ^ ib) >= 0) && (ia & 0x7fffffffffffffffll) != 0 && (ib & 0x7fffffffffffffffll) != 0;
+  const double r = (2.0 * a * b) * rcp_fp64(a + b);
+  return isel(ok, r, 0.0);
+}
+
 // ------------------------------------------------------------ Roe flux
 // Twice the Roe flux across a face with unit normal along one axis.  States
 // are ordered normal-first: q = (rho, m_n, m_t[0..NT-1], rho*e_t), where m_n

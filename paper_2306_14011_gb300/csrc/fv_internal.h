@@ -23,6 +23,8 @@ struct StageArgs {
   int ntile[3];        // tiles per axis
   int bc[3][2];        // FV_BC_* per axis side
   int use_tma;         // 1: stage tiles with TMA (tensor map valid), 0: plain loads
+  int limiter;         // FV_LIM_* of Eq. (6)
+  double cL, cR;       // unlimited kappa-scheme weights eps (1 -+ kappa) / 4
   double g1;           // gamma - 1
   double half_eps;     // eps / 2 (MUSCL slope weight)
   double efix;         // entropy-fix width / c~

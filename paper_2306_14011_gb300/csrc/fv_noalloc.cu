@@ -88,7 +88,8 @@ bool grid_ok(const fv_grid *g) {
 
 extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const double *U, double *R,
                                    double *rnorm2, void *stream) {
-  if (!grid_ok(g) || !s || !(s->gamma > 1.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0))
+  if (!grid_ok(g) || !s || !(s->gamma > 1.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0) ||
+      s->limiter < FV_LIM_MINMOD || s->limiter > FV_LIM_NONE)
     return FV_EINVAL;
   if (!U || !R || U == R || !device_pointer(U) || !device_pointer(R) || (rnorm2 && !device_pointer(rnorm2)))
     return FV_EINVAL;
@@ -139,6 +140,9 @@ extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const d
     a.half_inv_h[d] = 0.5 / h[d];
   }
   a.use_tma = 0;  // plain loads: no tensor map, results identical to the TMA loader
+  a.limiter = s->limiter;
+  a.cL = 0.25 * s->eps * (1.0 - s->kappa);
+  a.cR = 0.25 * s->eps * (1.0 + s->kappa);
   a.g1 = s->gamma - 1.0;
   a.half_eps = 0.5 * s->eps;
   a.efix = s->efix;

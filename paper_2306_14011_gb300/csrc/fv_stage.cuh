@@ -18,6 +18,7 @@
 // 1/tile_x + 1/tile_y [+ 1/tile_z] overhead); inside a tile each face is
 // evaluated once.
 #pragma once
+#include "../../include/fv.h"
 #include "fv_device.cuh"
 #include "fv_internal.h"
 
@@ -91,7 +92,27 @@ __device__ __forceinline__ void load_halo(double *tile, const StageArgs &a, cons
 
 // All face fluxes of the tile along axis D into F, then their differences
 // into the cell accumulator R (R = coef * dF for the first axis, += after).
-template <int DIM, int D>
+// MUSCL face states of Eq. (6) on the stencil q0..q3 for limiter LIM.  Both
+// limiters are symmetric (Psi(r) = r Psi(1/r)), so the two kappa-weighted
+// limited slopes coincide and the states are q -+ eps/2 * slope; without a
+// limiter the kappa weights cL = eps(1-kappa)/4, cR = eps(1+kappa)/4 apply.
+template <int LIM>
+__device__ __forceinline__ void muscl_states(double q0, double q1, double q2, double q3, double h, double cL,
+                                             double cR, double &QL, double &QR) {
+  const double dm = q1 - q0, d0 = q2 - q1, dp = q3 - q2;
+  if (LIM == FV_LIM_NONE) {
+    QL = fma(cL, dm, fma(cR, d0, q1));
+    QR = fma(-cR, d0, fma(-cL, dp, q2));
+  } else if (LIM == FV_LIM_VANLEER) {
+    QL = fma(h, vanleer(dm, d0), q1);
+    QR = fma(-h, vanleer(d0, dp), q2);
+  } else {
+    QL = fma(h, minmod(dm, d0), q1);
+    QR = fma(-h, minmod(d0, dp), q2);
+  }
+}
+
+template <int DIM, int D, int LIM>
 __device__ __forceinline__ void face_pass(const double *__restrict__ tile, double *__restrict__ F,
                                           double *__restrict__ R, const StageArgs &a, const int ext[3],
                                           const TileGeom &G, double coef) {
@@ -115,10 +136,7 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double *pv = p + v * G.plane;
-      const double q0 = pv[0], q1 = pv[sstride], q2 = pv[2 * sstride], q3 = pv[3 * sstride];
-      const double dm = q1 - q0, d0 = q2 - q1, dp = q3 - q2;
-      QL[v] = fma(h, minmod(dm, d0), q1);
-      QR[v] = fma(-h, minmod(d0, dp), q2);
+      muscl_states<LIM>(pv[0], pv[sstride], pv[2 * sstride], pv[3 * sstride], h, a.cL, a.cR, QL[v], QR[v]);
     }
     // normal-first ordering: (rho, m_D, tangential momenta, E)
     double qL[NT + 3], qR[NT + 3], Gf[NT + 3];
@@ -174,7 +192,7 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
 // the residual and write the epilogue.  `tile` is the CTA's dynamic shared
 // memory (128-byte aligned); s_coef and red are static shared scratch.
 // Returns false (uniformly across the CTA) if the tile load timed out.
-template <int DIM, int MODE>
+template <int DIM, int MODE, int LIM = FV_LIM_MINMOD>
 __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageArgs &a, int bx, int by, int bz,
                                           double *tile, uint64_t *mbar, uint32_t phase, double *s_coef,
                                           double (*red)[32]) {
@@ -238,9 +256,9 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
   }
   __syncthreads();
   const double dt = s_coef[0];
-  face_pass<DIM, 0>(tile, F, R, a, ext, G, s_coef[1]);
-  face_pass<DIM, 1>(tile, F, R, a, ext, G, s_coef[2]);
-  if constexpr (DIM == 3) face_pass<DIM, 2>(tile, F, R, a, ext, G, s_coef[3]);
+  face_pass<DIM, 0, LIM>(tile, F, R, a, ext, G, s_coef[1]);
+  face_pass<DIM, 1, LIM>(tile, F, R, a, ext, G, s_coef[2]);
+  if constexpr (DIM == 3) face_pass<DIM, 2, LIM>(tile, F, R, a, ext, G, s_coef[3]);
 
   // ---- 4. epilogue
   const int ncell = ext[0] * ext[1] * ext[2];
@@ -316,7 +334,7 @@ __device__ __forceinline__ double *aligned_smem(unsigned char *raw) {
 #ifndef FV_STAGE_MIN_BLOCKS
 #define FV_STAGE_MIN_BLOCKS 4
 #endif
-template <int DIM, int MODE>
+template <int DIM, int MODE, int LIM>
 __global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
   constexpr int NV = DIM + 2;
   extern __shared__ unsigned char smem_raw[];
@@ -336,32 +354,41 @@ __global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) stage_kernel(const _
   b /= a.ntile[0];
   const int by = b % a.ntile[1];
   const int bz = b / a.ntile[1];
-  tile_work<DIM, MODE>(&tmap, a, bx, by, bz, tile, mbar, 0u, s_coef, red);
+  tile_work<DIM, MODE, LIM>(&tmap, a, bx, by, bz, tile, mbar, 0u, s_coef, red);
 }
 
-template <int DIM>
-cudaError_t launch_stage_dim(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st) {
+template <int DIM, int LIM>
+cudaError_t launch_stage_lim(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st) {
   const size_t smem = stage_smem_bytes(DIM, a.tile);
   const long long nblk = (long long)a.ntile[0] * a.ntile[1] * a.ntile[2];
   const dim3 grid((unsigned)nblk), block(threads);
   switch (mode) {
-    case MODE_RESIDUAL: stage_kernel<DIM, MODE_RESIDUAL><<<grid, block, smem, st>>>(*tmap, a); break;
-    case MODE_STAGE1: stage_kernel<DIM, MODE_STAGE1><<<grid, block, smem, st>>>(*tmap, a); break;
-    case MODE_STAGE2: stage_kernel<DIM, MODE_STAGE2><<<grid, block, smem, st>>>(*tmap, a); break;
-    default: stage_kernel<DIM, MODE_STAGE3><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_RESIDUAL: stage_kernel<DIM, MODE_RESIDUAL, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_STAGE1: stage_kernel<DIM, MODE_STAGE1, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_STAGE2: stage_kernel<DIM, MODE_STAGE2, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
+    default: stage_kernel<DIM, MODE_STAGE3, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
   }
   return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t launch_stage_dim(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st) {
+  if (a.limiter == FV_LIM_VANLEER) return launch_stage_lim<DIM, FV_LIM_VANLEER>(mode, tmap, a, threads, st);
+  if (a.limiter == FV_LIM_NONE) return launch_stage_lim<DIM, FV_LIM_NONE>(mode, tmap, a, threads, st);
+  return launch_stage_lim<DIM, FV_LIM_MINMOD>(mode, tmap, a, threads, st);
 }
 
 // Allow each stage kernel the largest dynamic shared memory the device offers
 // (opt-in limit minus the kernel's static shared memory), so contexts with
 // different tile shapes never lower each other's limit.  `smem_optin` is the
 // device's per-block opt-in limit.
-template <int DIM>
-cudaError_t set_stage_attributes_dim(size_t smem_optin) {
+template <int DIM, int LIM>
+cudaError_t set_stage_attributes_lim(size_t smem_optin) {
   cudaError_t e = cudaSuccess;
-  const void *k[4] = {(const void *)stage_kernel<DIM, MODE_RESIDUAL>, (const void *)stage_kernel<DIM, MODE_STAGE1>,
-                      (const void *)stage_kernel<DIM, MODE_STAGE2>, (const void *)stage_kernel<DIM, MODE_STAGE3>};
+  const void *k[4] = {(const void *)stage_kernel<DIM, MODE_RESIDUAL, LIM>,
+                      (const void *)stage_kernel<DIM, MODE_STAGE1, LIM>,
+                      (const void *)stage_kernel<DIM, MODE_STAGE2, LIM>,
+                      (const void *)stage_kernel<DIM, MODE_STAGE3, LIM>};
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, k[i]);
@@ -369,6 +396,14 @@ cudaError_t set_stage_attributes_dim(size_t smem_optin) {
       e = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(smem_optin - fa.sharedSizeBytes));
   }
+  return e;
+}
+
+template <int DIM>
+cudaError_t set_stage_attributes_dim(size_t smem_optin) {
+  cudaError_t e = set_stage_attributes_lim<DIM, FV_LIM_MINMOD>(smem_optin);
+  if (e == cudaSuccess) e = set_stage_attributes_lim<DIM, FV_LIM_VANLEER>(smem_optin);
+  if (e == cudaSuccess) e = set_stage_attributes_lim<DIM, FV_LIM_NONE>(smem_optin);
   return e;
 }
 

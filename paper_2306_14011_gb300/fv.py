@@ -36,9 +36,12 @@ class fv_grid(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("len", C.c_double * 3), ("bc", (C.c_int * 2) * 3)]
 
 
+FV_LIM_MINMOD, FV_LIM_VANLEER, FV_LIM_NONE = 0, 1, 2
+
+
 class fv_scheme(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("eps", C.c_double), ("kappa", C.c_double),
-                ("efix", C.c_double)]
+                ("efix", C.c_double), ("limiter", C.c_int)]
 
 
 class fv_kernel_cfg(C.Structure):
@@ -140,8 +143,8 @@ def make_grid(g) -> fv_grid:
     return G
 
 
-def make_scheme(gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1) -> fv_scheme:
-    return fv_scheme(gamma, cfl, eps, kappa, efix)
+def make_scheme(gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, limiter=FV_LIM_MINMOD) -> fv_scheme:
+    return fv_scheme(gamma, cfl, eps, kappa, efix, limiter)
 
 
 def launch_to_dict(l: fv_launch) -> dict:
@@ -346,15 +349,17 @@ class Solver:
     """A libfv context for one grid.
 
     Solver(grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1,
-           launch=None (dict or fv_launch), stream=None (torch's current stream))
+           launch=None (dict or fv_launch), stream=None (torch's current stream),
+           limiter=FV_LIM_MINMOD | FV_LIM_VANLEER | FV_LIM_NONE)
     """
 
-    def __init__(self, grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, launch=None, stream=None):
+    def __init__(self, grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, launch=None, stream=None,
+                 limiter=FV_LIM_MINMOD):
         self.batched = isinstance(grid, (list, tuple))
         self.grids = list(grid) if self.batched else [grid]
         self.grid = self.grids[0]
         self.ngrids = len(self.grids)
-        self.scheme = make_scheme(gamma, cfl, eps, kappa, efix)
+        self.scheme = make_scheme(gamma, cfl, eps, kappa, efix, limiter)
         if isinstance(launch, dict):
             launch = launch_from_dict(launch)
         self.ctx = fv_init(grid, self.scheme, launch, stream)

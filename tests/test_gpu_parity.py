@@ -49,13 +49,13 @@ def relerr(a, b):
     return worst
 
 
-def assert_residual_parity(g, U, R, cells=None, tag=""):
+def assert_residual_parity(g, U, R, cells=None, tag="", s=None):
     """R: GPU residual, full (nvar, ...) array, or (len(cells), nvar) when cells
     is given.  Checked against the FP64 oracle and its extended-precision
-    evaluation (see the module docstring for the bar)."""
+    evaluation (see the module docstring for the bar); s: oracle scheme."""
     if cells is None:
-        Ro = O.residual(g, U).reshape(g.nvar, -1)
-        Rx = O.residual_ext(g, U).reshape(g.nvar, -1)
+        Ro = O.residual(g, U, s).reshape(g.nvar, -1)
+        Rx = O.residual_ext(g, U, s).reshape(g.nvar, -1)
         Rg = np.asarray(R).reshape(g.nvar, -1)
     else:
         Ro = O.residual_cells(g, U, cells).T
@@ -364,3 +364,39 @@ def test_graph_cache_eviction_keeps_results_identical():
         s.run(keep[0], 20)  # an evicted pointer is captured again
         s.run(ref, 20)
         assert torch.equal(keep[0], ref)
+
+
+@pytest.mark.parametrize("lim,kappa", [(fv.FV_LIM_VANLEER, -1.0), (fv.FV_LIM_NONE, 1.0 / 3.0), (fv.FV_LIM_NONE, 0.0),
+                                       (fv.FV_LIM_NONE, -1.0), (fv.FV_LIM_NONE, 1.0)])
+@pytest.mark.parametrize("case", ["vortex128", "ragged70x45_mixed_bc", "tgv24", "box3d_10x7x9_transmissive"])
+def test_limiter_variants_match_oracle(case, lim, kappa):
+    """Eq. (6) with van Leer's limiter or without a limiter (kappa-scheme)."""
+    g, U = CASES[case]()
+    so = O.scheme(limiter=lim, kappa=kappa)
+    with fv.Solver(g, limiter=lim, kappa=kappa) as s:
+        R = s.residual(dev(U)).cpu().numpy()
+        dto = O.time_step(g, U, so)
+        Ud = dev(U)
+        s.rk_step(Ud, dto)
+        U1 = Ud.cpu().numpy()
+        R_noalloc = torch.empty_like(dev(U))
+        fv.fv_residual_noalloc(g, s.scheme, dev(U), R_noalloc)
+        torch.cuda.synchronize()
+    assert_residual_parity(g, U, R, tag=f"{case}-lim{lim}-k{kappa}", s=so)
+    assert np.array_equal(R_noalloc.cpu().numpy(), R)
+    Uo, _ = O.rk3_step(g, U, dto, so)
+    assert relerr(U1, Uo) <= TOL_RES
+
+
+def test_limiter_variants_unsupported_where_documented():
+    g, U = I.isentropic_vortex(32)
+    with pytest.raises(fv.FvError) as e:
+        fv.Solver([g, g], limiter=fv.FV_LIM_VANLEER)
+    assert e.value.status == fv.FV_EUNSUPPORTED
+    with fv.Solver(g, limiter=fv.FV_LIM_NONE, kappa=1.0 / 3.0) as s:
+        with pytest.raises(fv.FvError) as e:
+            s.residual_vjp(dev(U), dev(U))
+        assert e.value.status == fv.FV_EUNSUPPORTED
+    with pytest.raises(fv.FvError) as e:
+        fv.Solver(g, limiter=7)
+    assert e.value.status == fv.FV_EINVAL

@@ -377,3 +377,66 @@ def test_fp64_oracle_is_within_rounding_of_extended_precision():
     # extended precision is the same definition: it reproduces free-stream zeros
     gz = I.grid2d(9, 6, 1.0, 1.0)
     assert np.all(O.residual_ext(gz, I.uniform_state(gz)) == 0.0)
+
+
+# ------------------------------------------------------------------ scheme variants of Eq. (6)
+
+def test_unlimited_kappa_schemes_on_polynomials():
+    """Without a limiter Eq. (6) is the kappa-scheme: exact face values of
+    linear data for every kappa; kappa = 1/3 reproduces the face values of a
+    quadratic from its cell averages (third order); kappa = 1 is the central
+    average of the two neighbours."""
+    for kappa in (-1.0, 0.0, 1.0 / 3.0, 1.0):
+        s = O.scheme(limiter=O.LIM_NONE, kappa=kappa)
+        QL, QR = O.muscl([1.0, 1.5, 2.0, 2.5], s)
+        assert abs(QL - 1.75) < 1e-15 and abs(QR - 1.75) < 1e-15
+    s = O.scheme(limiter=O.LIM_NONE, kappa=1.0 / 3.0)
+    for k in range(-3, 4):
+        avg = [(k + j) ** 2 + 1.0 / 12.0 for j in (-1, 0, 1, 2)]  # cell averages of x^2, unit cells
+        QL, QR = O.muscl(avg, s)
+        exact = (k + 0.5) ** 2
+        assert abs(QL - exact) < 1e-13 and abs(QR - exact) < 1e-13
+    QL, QR = O.muscl([0.0, 1.0, 3.0, 7.0], O.scheme(limiter=O.LIM_NONE, kappa=1.0))
+    assert QL == 2.0 and QR == 2.0
+    # kappa = -1: fully upwind, QL extrapolates from the left pair only
+    QL, QR = O.muscl([0.0, 1.0, 3.0, 7.0], O.scheme(limiter=O.LIM_NONE, kappa=-1.0))
+    assert QL == 1.5 and QR == 1.0
+
+
+def test_van_leer_limiter():
+    s = O.scheme(limiter=O.LIM_VANLEER)
+    rng = np.random.default_rng(3)
+    psi = lambda r: (r + abs(r)) / (1.0 + abs(r))
+    for _ in range(300):
+        q = rng.normal(size=4)
+        QL, QR = O.muscl(q, s)
+        dm, d0, dp = q[1] - q[0], q[2] - q[1], q[3] - q[2]
+        # ratio form of Eq. (6), kappa-independent for this symmetric limiter
+        assert abs(QL - (q[1] + 0.5 * psi(d0 / dm) * dm)) <= 1e-14 * max(1, abs(QL))
+        assert abs(QR - (q[2] - 0.5 * psi(d0 / dp) * dp)) <= 1e-14 * max(1, abs(QR))
+        alt = O.muscl(q, O.scheme(limiter=O.LIM_VANLEER, kappa=0.5))
+        assert abs(alt[0] - QL) <= 4e-16 * max(1, abs(QL)) and abs(alt[1] - QR) <= 4e-16 * max(1, abs(QR))
+        # TVD: face states stay between the two cells of the face
+        assert min(q[1], q[2]) - 1e-15 <= QL <= max(q[1], q[2]) + 1e-15
+    assert O.muscl([1.0, 1.5, 2.0, 2.5], s) == (1.75, 1.75)
+
+
+def test_limiter_variants_conserve_and_converge():
+    g, U = I.isentropic_vortex(32, noise=0.0)
+    for lim, kappa in ((O.LIM_VANLEER, -1.0), (O.LIM_NONE, 1.0 / 3.0)):
+        s = O.scheme(limiter=lim, kappa=kappa)
+        R = O.residual(g, U, s)
+        assert np.all(np.abs(R.reshape(4, -1).sum(axis=1)) < 1e-13 * np.abs(R).max() * g.ncells)
+    errs = {}
+    for lim, kappa in ((O.LIM_MINMOD, -1.0), (O.LIM_VANLEER, -1.0), (O.LIM_NONE, 1.0 / 3.0)):
+        e = []
+        for N in (32, 64):
+            g, U = I.isentropic_vortex(N, noise=0.0)
+            U1, _ = O.run(g, U, 100000, t_end=1.0, s=O.scheme(limiter=lim, kappa=kappa))
+            _, Ue = I.isentropic_vortex(N, noise=0.0, t=1.0)
+            e.append(np.abs(U1[0] - Ue[0]).mean())
+        errs[lim] = e
+        assert np.log2(e[0] / e[1]) > 1.6, (lim, e)
+    # the smoother limiter and the unlimited third-order scheme beat minmod on smooth data
+    assert errs[O.LIM_VANLEER][1] < errs[O.LIM_MINMOD][1]
+    assert errs[O.LIM_NONE][1] < errs[O.LIM_MINMOD][1]
