@@ -87,13 +87,17 @@ enum { FV_LOADER_TMA = 0, FV_LOADER_PLAIN = 1 };
  * FV_LOADER_TMA stages tiles with TMA when the grid allows it (even nx, a
  * 16-byte aligned state, tile + halo no larger than the grid) and falls back
  * to plain loads otherwise, FV_LOADER_PLAIN always uses plain loads.
+ * march (3D only): 0 = box tiles of tile[0] x tile[1] x tile[2] cells;
+ * 1 = x-y tiles of tile[0] x tile[1] columns that march along z through
+ * chunks of tile[2] planes (1..nz), computing every z-face once per chunk.
  * Time-step reduction: threads per CTA (32..1024) and grid = number of CTAs
- * (0 = two per SM); tile and loader are ignored. */
+ * (0 = two per SM); tile, loader and march are ignored. */
 typedef struct fv_kernel_cfg {
   int tile[3];
   int threads;
   int grid;
   int loader;
+  int march;
 } fv_kernel_cfg;
 
 /* stage[s]: RK stage s+1 (fv_residual uses stage[0]); dt: time-step reduction. */
@@ -105,7 +109,10 @@ typedef struct fv_launch {
 typedef struct fv_ctx fv_ctx;
 
 /* Fill *l with the default launch configuration for grid g (one tile shape
- * and thread count for all stages).  Returns FV_EINVAL for a bad grid. */
+ * and thread count for all stages): 2D 32x31 box tiles (32x32 when 31-row
+ * tiles would pad the last tile row by over 1% more cells) with 256 threads;
+ * 3D 8x8x8 box tiles with 192 threads; time-step reduction 256 threads, two
+ * CTAs per SM.  Returns FV_EINVAL for a bad grid. */
 int fv_default_launch(const fv_grid *g, fv_launch *l);
 
 /* Create a solver context for ngrids grids.  ngrids = 1: one grid, 2D or 3D.
@@ -284,7 +291,7 @@ int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *b
  * library's device image -- every GPU that loads libfv holds it until the
  * process exits -- holding nvar partial sums per tile.  With rnorm2 != NULL
  * the grid may have at most 131072 / nvar default tiles (2D: 32768 tiles of
- * 32x16 cells, e.g. 4096 x 4096; 3D: 26214 tiles of 16x8x4 cells); larger
+ * 32x31 or 32x32 cells, e.g. 5696 x 5696; 3D: 26214 tiles of 8x8x8 cells); larger
  * grids return FV_EINVAL before anything is launched.  The first call on each
  * device looks up the scratch array's device address (cudaGetSymbolAddress)
  * and sets kernel attributes: make that first call before any stream capture.

@@ -135,8 +135,11 @@ int validate_scheme(const fv_scheme *s) {
 int validate_launch(const fv_grid *g, const fv_launch *l, size_t smem_optin) {
   for (int s = 0; s < 3; ++s) {
     const fv_kernel_cfg &k = l->stage[s];
+    if (k.march != 0 && (k.march != 1 || g->dim != 3)) return FV_EINVAL;
     for (int d = 0; d < 3; ++d) {
-      if (d < g->dim) {
+      if (d == 2 && k.march) {
+        if (k.tile[2] < 1 || k.tile[2] > (1 << 24)) return FV_EINVAL;  // planes per chunk
+      } else if (d < g->dim) {
         if (k.tile[d] < 2 || k.tile[d] > 252) return FV_EINVAL;
       } else if (k.tile[d] != 1) {
         return FV_EINVAL;
@@ -146,7 +149,8 @@ int validate_launch(const fv_grid *g, const fv_launch *l, size_t smem_optin) {
     if (k.threads < 32 || k.threads > 256 || k.threads % 32) return FV_EINVAL;
     if (k.grid != 0) return FV_EINVAL;  // tiled kernels cover the domain
     if (k.loader != FV_LOADER_TMA && k.loader != FV_LOADER_PLAIN) return FV_EINVAL;
-    if (stage_smem_bytes(g->dim, k.tile) + kStaticSmemReserve > smem_optin) return FV_EINVAL;
+    const size_t smem = k.march ? march_smem_bytes(k.tile) : stage_smem_bytes(g->dim, k.tile);
+    if (smem + kStaticSmemReserve > smem_optin) return FV_EINVAL;
   }
   if (l->dt.threads < 32 || l->dt.threads > 1024 || l->dt.threads % 32 || l->dt.grid < 0) return FV_EINVAL;
   return FV_OK;
@@ -156,14 +160,15 @@ void ntiles(const fv_grid &g, const int tile[3], int nt[3]) {
   for (int d = 0; d < 3; ++d) nt[d] = (d < g.dim) ? (g.n[d] + tile[d] - 1) / tile[d] : 1;
 }
 
-// TMA tensor map over a state array: dims (x, y[, z], var), box = tile + halo.
-bool make_tmap(const fv_ctx *c, const double *U, const int tile[3], CUtensorMap *map) {
+// TMA tensor map over a state array: dims (x, y[, z], var), box = tile + halo
+// (one z-plane for the z-marching kernel).
+bool make_tmap(const fv_ctx *c, const double *U, const int tile[3], int march, CUtensorMap *map) {
   const fv_grid &g = c->grid;
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   if (g.n[0] % 2) return false;                          // row stride must be a multiple of 16 bytes
   if (reinterpret_cast<uintptr_t>(U) % 16) return false;  // base address alignment
-  const int box[3] = {tile[0] + 4, tile[1] + 4, tile[2] + 4};
+  const int box[3] = {tile[0] + 4, tile[1] + 4, march ? 1 : tile[2] + 4};
   for (int d = 0; d < g.dim; ++d)
     if (box[d] > 256 || box[d] > g.n[d]) return false;
   cuuint64_t dims[4], strides[3];
@@ -224,7 +229,8 @@ int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, dou
   a.flags = c->flags;
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
-  a.use_tma = (k.loader == FV_LOADER_TMA && make_tmap(c, Us, k.tile, &map)) ? 1 : 0;
+  a.march = k.march;
+  a.use_tma = (k.loader == FV_LOADER_TMA && make_tmap(c, Us, k.tile, k.march, &map)) ? 1 : 0;
   FV_CK(launch_stage(g.dim, mode, &map, a, k.threads, st));
   return FV_OK;
 }
@@ -510,15 +516,21 @@ int fv_default_launch(const fv_grid *g, fv_launch *l) {
   for (int s = 0; s < 3; ++s) {
     fv_kernel_cfg &k = l->stage[s];
     if (g->dim == 2) {
+      // 32 x 31 tiles have 33 x 31 x-faces and 32 x 32 y-faces: four full
+      // rounds of 256 threads each (about 1% faster than 32 x 32 tiles).  Take
+      // 32 rows instead when 31-row tiles would leave over 1% more padding
+      // cells in the ragged last tile row.
+      const long long n1 = g->n[1];
+      const long long pad31 = (n1 + 30) / 31 * 31 - n1, pad32 = (n1 + 31) / 32 * 32 - n1;
       k.tile[0] = 32;
-      k.tile[1] = 16;
+      k.tile[1] = (100 * pad31 < 100 * pad32 + n1) ? 31 : 32;
       k.tile[2] = 1;
     } else {
-      k.tile[0] = 16;
+      k.tile[0] = 8;  // 9 x 8 x 8 faces per axis: three full rounds of 192 threads
       k.tile[1] = 8;
-      k.tile[2] = 4;
+      k.tile[2] = 8;
     }
-    k.threads = 256;
+    k.threads = g->dim == 2 ? 256 : 192;
     k.grid = 0;
   }
   l->dt.threads = 256;

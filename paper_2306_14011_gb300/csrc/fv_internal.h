@@ -23,6 +23,7 @@ struct StageArgs {
   int ntile[3];        // tiles per axis
   int bc[3][2];        // FV_BC_* per axis side
   int use_tma;         // 1: stage tiles with TMA (tensor map valid), 0: plain loads
+  int march;           // 3D: 1 = x-y tiles marching along z in chunks of tile[2] planes
   int limiter;         // FV_LIM_* of Eq. (6)
   double cL, cR;       // unlimited kappa-scheme weights eps (1 -+ kappa) / 4
   double g1;           // gamma - 1
@@ -93,6 +94,13 @@ cudaError_t launch_batch_run(const BatchArgs &b, int blocks, int threads, size_t
 
 // Dynamic shared memory of a stage-kernel CTA for a tile shape.
 size_t stage_smem_bytes(int dim, const int tile[3]);
+// ... and of the z-marching 3D kernel (tile[2] = planes per chunk, unused here).
+size_t march_smem_bytes(const int tile[3]);
+
+// The z-marching 3D stage kernel (StageArgs.march = 1): launcher and the
+// dynamic shared-memory attribute of its instantiations.
+cudaError_t launch_march(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st);
+cudaError_t set_march_attributes(size_t smem_optin);
 
 // Kernel launchers (return the launch error).
 cudaError_t launch_stage(int dim, int mode, const CUtensorMap *tmap, const StageArgs &a, int threads,

@@ -140,6 +140,7 @@ extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const d
     a.half_inv_h[d] = 0.5 / h[d];
   }
   a.use_tma = 0;  // plain loads: no tensor map, results identical to the TMA loader
+  a.march = k.march;
   a.limiter = s->limiter;
   a.cL = 0.25 * s->eps * (1.0 - s->kappa);
   a.cR = 0.25 * s->eps * (1.0 + s->kappa);

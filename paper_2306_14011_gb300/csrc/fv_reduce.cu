@@ -19,11 +19,14 @@ cudaError_t set_stage_attributes_3d(size_t);
 
 cudaError_t launch_stage(int dim, int mode, const CUtensorMap *tmap, const StageArgs &a, int threads,
                          cudaStream_t st) {
-  return dim == 2 ? launch_stage_2d(mode, tmap, a, threads, st) : launch_stage_3d(mode, tmap, a, threads, st);
+  if (dim == 2) return launch_stage_2d(mode, tmap, a, threads, st);
+  return a.march ? launch_march(mode, tmap, a, threads, st) : launch_stage_3d(mode, tmap, a, threads, st);
 }
 
 cudaError_t stage_kernel_attributes(int dim, size_t smem) {
-  return dim == 2 ? set_stage_attributes_2d(smem) : set_stage_attributes_3d(smem);
+  if (dim == 2) return set_stage_attributes_2d(smem);
+  const cudaError_t e = set_stage_attributes_3d(smem);
+  return e == cudaSuccess ? set_march_attributes(smem) : e;
 }
 
 // Maximum over cells of sum_d (|u_d| + c) / dx_d, c = sqrt(gamma p / rho),

@@ -59,8 +59,9 @@ Space make_space(int dim) {
     }
     sp.vals.push_back(threads);
     sp.vals.push_back({FV_LOADER_TMA, FV_LOADER_PLAIN});
+    if (dim == 3) sp.vals.push_back({0, 1});  // box tiles / z-marching (chunk = 8 x tile-z value)
   }
-  sp.per_stage = dim == 2 ? 4 : 5;
+  sp.per_stage = dim == 2 ? 4 : 6;
   sp.vals.push_back({128, 256, 512, 1024});  // time-step kernel threads
   sp.vals.push_back({1, 2, 4, 8});           // time-step kernel CTAs per SM
   sp.nparams = (int)sp.vals.size();
@@ -81,6 +82,8 @@ fv_launch to_launch(const Space &sp, const Cfg &c, int sms) {
     const int o = sp.dim == 3 ? 3 : 2;
     k.threads = sp.vals[b + o][c[b + o]];
     k.loader = sp.vals[b + o + 1][c[b + o + 1]];
+    k.march = sp.dim == 3 ? sp.vals[b + o + 2][c[b + o + 2]] : 0;
+    if (k.march) k.tile[2] *= 8;  // planes per chunk: 16, 32 or 64
     k.grid = 0;
   }
   const int b = 3 * sp.per_stage;
@@ -90,11 +93,11 @@ fv_launch to_launch(const Space &sp, const Cfg &c, int sms) {
 }
 
 // Features: log2 of the power-of-two parameters (tiles, thread counts, grid
-// multiplier), the loader as 0/1.
+// multiplier), the loader and the 3D kernel choice as 0/1.
 void features(const Space &sp, const Cfg &c, double *f) {
   for (int p = 0; p < sp.nparams; ++p) {
     const int v = sp.vals[p][c[p]];
-    f[p] = (sp.vals[p].size() == 2 && sp.vals[p][0] == FV_LOADER_TMA) ? (double)v : std::log2((double)v);
+    f[p] = (sp.vals[p].size() == 2 && sp.vals[p][0] == 0) ? (double)v : std::log2((double)v);
   }
 }
 
@@ -375,6 +378,7 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
               l.stage[s].tile[2] = dim == 3 ? cz : 1;
               l.stage[s].threads = th;
               l.stage[s].loader = FV_LOADER_TMA;
+              l.stage[s].march = 0;
             }
             double t = 0.0;
             r = ctx_time_launch(ctx, Uw, &l, o.steps, o.repeats, &t);

@@ -45,7 +45,8 @@ class fv_scheme(C.Structure):
 
 
 class fv_kernel_cfg(C.Structure):
-    _fields_ = [("tile", C.c_int * 3), ("threads", C.c_int), ("grid", C.c_int), ("loader", C.c_int)]
+    _fields_ = [("tile", C.c_int * 3), ("threads", C.c_int), ("grid", C.c_int), ("loader", C.c_int),
+                ("march", C.c_int)]
 
 
 class fv_launch(C.Structure):
@@ -148,7 +149,8 @@ def make_scheme(gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, limiter=FV_LI
 
 
 def launch_to_dict(l: fv_launch) -> dict:
-    st = [dict(tile=tuple(l.stage[s].tile), threads=l.stage[s].threads, loader=l.stage[s].loader) for s in range(3)]
+    st = [dict(tile=tuple(l.stage[s].tile), threads=l.stage[s].threads, loader=l.stage[s].loader,
+               march=l.stage[s].march) for s in range(3)]
     return dict(stage=st, dt=dict(threads=l.dt.threads, grid=l.dt.grid))
 
 
@@ -161,6 +163,7 @@ def launch_from_dict(d: dict) -> fv_launch:
         l.stage[s].threads = e["threads"]
         l.stage[s].grid = 0
         l.stage[s].loader = e.get("loader", FV_LOADER_TMA)
+        l.stage[s].march = e.get("march", 0)
     l.dt.threads = d["dt"]["threads"]
     l.dt.grid = d["dt"].get("grid", 0)
     return l

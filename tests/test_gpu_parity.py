@@ -282,13 +282,19 @@ def test_refined_rsqrt_and_reciprocal_are_within_two_ulp():
 def _sample_cells(g, rng, k):
     n = g.n
     cells = list(rng.integers(0, g.ncells, k))
-    # domain corners and edges, and cells around tile boundaries of the default launch
-    for x in (0, 1, 2, 15, 16, 31, 32, 33, n[0] - 2, n[0] - 1):
-        for y in (0, 1, 15, 16, 17, n[1] - 2, n[1] - 1):
+    # domain corners and edges, and cells on both sides of the first two tile
+    # boundaries of the default launch along each axis
+    t = fv.fv_default_launch(g).stage[0].tile
+
+    def near(d):
+        return sorted({0, 1, 2, t[d] - 1, t[d], t[d] + 1, 2 * t[d] - 1, 2 * t[d], n[d] - 2, n[d] - 1})
+
+    for x in near(0):
+        for y in near(1):
             if g.dim == 2:
                 cells.append(y * n[0] + x)
             else:
-                for z in (0, 3, 4, n[2] - 1):
+                for z in near(2):
                     cells.append((z * n[1] + y) * n[0] + x)
     return np.unique(np.array(cells, dtype=np.int64))
 
