@@ -22,7 +22,7 @@ SOURCES = ["fv_api.cu", "fv_reduce.cu", "fv_stage2d.cu", "fv_stage3d.cu", "fv_no
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 # Resident 256-thread CTAs per SM the stage kernels' register budget targets
-# (4 = 64 registers per thread).
+# (default 2 = up to 128 registers per thread; 4 = 64).
 MIN_BLOCKS = os.environ.get("FV_STAGE_MIN_BLOCKS")
 if MIN_BLOCKS:
     FLAGS += [f"-DFV_STAGE_MIN_BLOCKS={int(MIN_BLOCKS)}"]

@@ -24,7 +24,9 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
                                            double efix, double inv2efix, const double (&Gb)[NT + 3],
                                            double (&QLb)[NT + 3], double (&QRb)[NT + 3]) {
   constexpr int E = NT + 2;
-  // ---------------- forward (as in roe_2F)
+  // ---------------- forward: the flux of roe_2F, with the Roe averages in
+  // their two-weight form u~ = wL uL + wR uR, H~ = wL HL + wR HR (the same
+  // function; roe_2F rearranges it to save FP64 operations)
   const double tL = rsqrt_fp64(QL[0]);
   const double rL = tL * tL;
   const double sL = QL[0] * tL;

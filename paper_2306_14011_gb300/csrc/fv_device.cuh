@@ -50,6 +50,20 @@ __device__ __forceinline__ double minmod(double a, double b) {
   return __longlong_as_double(((ia ^ ib) < 0) ? 0ll : m);
 }
 
+// x / 2 for x >= 0 on the integer pipe: decrement the biased exponent.  Exact
+// (bitwise equal to 0.5 * x) for x = 0, inf, NaN and every normal x of
+// exponent field >= 2; the rest (0 < x < 2^-1021, never reached by the squared
+// speeds and inverse squared sound speeds it is used on) take the FP64
+// multiply in a warp-uniform branch.
+__device__ __forceinline__ double half_nonneg(double x) {
+  const long long b = dbits(x);
+  const bool normal = b >= (2ll << 52) && b < 0x7ff0000000000000ll;
+  const bool tiny = b > 0 && b < (2ll << 52);
+  double h = __longlong_as_double(normal ? b - (1ll << 52) : (b <= 0 ? 0ll : b));
+  if (__any_sync(__activemask(), tiny)) h = isel(tiny, 0.5 * x, h);
+  return h;
+}
+
 // true when x is not a finite positive double (x <= 0, -0, inf or NaN).
 __device__ __forceinline__ bool not_positive_finite(double x) {
   const long long ix = dbits(x);
@@ -127,7 +141,6 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   }
   const double pL = g1 * fma(-0.5, kL, QL[E]);
   const double eL = QL[E] + pL;  // rho h_t
-  const double HL = eL * rL;
   // right primitives
   const double tR = rsqrt_fp64(QR[0]);
   const double rR = tR * tR;
@@ -142,22 +155,25 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   }
   const double pR = g1 * fma(-0.5, kR, QR[E]);
   const double eR = QR[E] + pR;
-  const double HR = eR * rR;
 
-  // Roe averages with sqrt(rho) weights
+  // Roe averages with sqrt(rho) weights wL = sL / (sL + sR), wR = 1 - wL:
+  // u~ = uR - wL (uR - uL) reuses the velocity jumps of the wave strengths,
+  // and H~ = (sL HL + sR HR) / (sL + sR) with sL HL = eL / sL = eL tL
   const double inv = rcp_fp64(sL + sR);
-  const double wL = sL * inv, wR = sR * inv;
-  const double un = fma(wL, unL, wR * unR);
-  double ut[NT];
+  const double wL = sL * inv;
+  const double dun = unR - unL;
+  const double un = fma(-wL, dun, unR);
+  double ut[NT], dut[NT];
   double q2 = un * un;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    ut[t] = fma(wL, utL[t], wR * utR[t]);
+    dut[t] = utR[t] - utL[t];
+    ut[t] = fma(-wL, dut[t], utR[t]);
     q2 = fma(ut[t], ut[t], q2);
   }
-  const double H = fma(wL, HL, wR * HR);
+  const double H = fma(eL, tL, eR * tR) * inv;
   const double rho = sL * sR;
-  const double hq = 0.5 * q2;
+  const double hq = half_nonneg(q2);
   const double c2 = g1 * (H - hq);
   const double tc = rsqrt_fp64(c2);  // 1/c~
   const double c = c2 * tc;
@@ -166,9 +182,8 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   // wave strengths
   const double drho = QR[0] - QL[0];
   const double dp = pR - pL;
-  const double dun = unR - unL;
   const double rcdun = (rho * c) * dun;
-  const double hic2 = 0.5 * ic2;
+  const double hic2 = half_nonneg(ic2);
   const double a1 = (dp - rcdun) * hic2;
   const double a3 = (dp + rcdun) * hic2;
   const double a2 = fma(-dp, ic2, drho);
@@ -198,7 +213,7 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   double Dt[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    const double B = lr * (utR[t] - utL[t]);
+    const double B = lr * dut[t];
     Dt[t] = fma(ut[t], D0, B);
     DE = fma(ut[t], B, DE);
   }

@@ -328,11 +328,10 @@ __device__ __forceinline__ double *aligned_smem(unsigned char *raw) {
 }
 
 // One CTA per tile of the grid.  Register budget: FV_STAGE_MIN_BLOCKS resident
-// 256-thread CTAs per SM (4 by default: 64 registers per thread; the default
-// 2D tile's shared memory also allows four).  More warps per SM hide the phase
-// barriers; the FP64 instruction count does not depend on the budget.
+// 256-thread CTAs per SM (2 by default: up to 128 registers per thread, no
+// spills; the default tiles' shared memory also allows two CTAs per SM).
 #ifndef FV_STAGE_MIN_BLOCKS
-#define FV_STAGE_MIN_BLOCKS 4
+#define FV_STAGE_MIN_BLOCKS 2
 #endif
 template <int DIM, int MODE, int LIM>
 __global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
