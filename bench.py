@@ -50,9 +50,10 @@ BYTES_PER_CELL_STAGE_3D = 320.0 / 3.0
 # (a DFMA loop measured 1.18 TFLOP/s on this part).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one stage-kernel launch from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, full 4096^2 launch), valid for the kernel sources
-# whose hash is recorded with it; null otherwise.
-STAGE_TRAFFIC = {"bytes": None, "source_hash": None}
+# dram__bytes_write.sum, full 4096^2 launches, mean of the three stages of one
+# step), valid for the kernel sources whose hash is recorded with it; null
+# otherwise.
+STAGE_TRAFFIC = {"bytes": 1.3913e9, "source_hash": "f1100ee232bd7c88"}
 
 
 def kernel_source_hash() -> str:
@@ -297,7 +298,7 @@ def make_workload(args, I):
         n = args.n
         g, U0 = I.kelvin_helmholtz(n, seed=1)
         return dict(name="kh4096", grid=g, U0=U0, cells=g.ncells, batched=False, flop=FLOP_PER_CELL_STAGE_2D,
-                    bytes=BYTES_PER_CELL_STAGE_2D, kernel="fvk::stage_kernel<2, stage>", launches_per_step=4,
+                    bytes=BYTES_PER_CELL_STAGE_2D, kernel="fvk::stage_kernel<2, stage>", launches_per_step=5,
                     metric=METRIC,
                     desc=f"2D Euler Kelvin-Helmholtz {n}x{n} periodic, FP64, MUSCL-minmod + Roe + SSP-RK3, CFL 0.5; "
                          f"1 bench step = 1 SSP-RK3 step (dt reduction + 3 fused stage kernels) replayed from a "
@@ -307,7 +308,7 @@ def make_workload(args, I):
         n = 384 if args.n == N_CELLS_SIDE else args.n
         g, U0 = I.taylor_green(n, seed=2)
         return dict(name="tgv384", grid=g, U0=U0, cells=g.ncells, batched=False, flop=FLOP_PER_CELL_STAGE_3D,
-                    bytes=BYTES_PER_CELL_STAGE_3D, kernel="fvk::stage_kernel<3, stage>", launches_per_step=4,
+                    bytes=BYTES_PER_CELL_STAGE_3D, kernel="fvk::stage_kernel<3, stage>", launches_per_step=5,
                     metric=f"FP64 cell-updates/s per RK stage (3D Euler Taylor-Green {n}^3)",
                     desc=f"3D Euler Taylor-Green {n}^3 periodic, M=0.1, 1e-4 pressure noise, FP64, MUSCL-minmod + "
                          f"Roe + SSP-RK3, CFL 0.5; 1 bench step = 1 SSP-RK3 step replayed from a CUDA graph",

@@ -82,8 +82,9 @@ enum { FV_LOADER_TMA = 0, FV_LOADER_PLAIN = 1 };
 
 /* Launch parameters of one kernel: the tunables of the autotuner.
  * Tiled kernels (residual and RK stages): cells per CTA tile (tile[0] even,
- * 2..252 per axis, tile[2] = 1 in 2D), threads per CTA (32..256, a multiple
- * of 32); grid must be 0 (one CTA per tile covers the domain); loader
+ * 2..252 per axis, tile[2] = 1 in 2D), threads per CTA (a multiple of 32,
+ * 32..256; 32..192 for 3D box tiles); grid must be 0 (one CTA per tile covers
+ * the domain); loader
  * FV_LOADER_TMA stages tiles with TMA when the grid allows it (even nx, a
  * 16-byte aligned state, tile + halo no larger than the grid) and falls back
  * to plain loads otherwise, FV_LOADER_PLAIN always uses plain loads.

@@ -81,6 +81,7 @@ struct fv_ctx {
   double *U1, *U2;            // RK stage buffers
   double *stage_in, *stage_out;  // host-pointer staging (lazy)
   unsigned long long *smax;   // scratch: bits of the max wave-speed sum
+  unsigned *lbound;           // scratch: bits of its certified FP32 lower bound
   unsigned *flags;            // scratch: device flags
   double *t_acc;              // scratch: simulated time
   double *dt_dev;             // scratch: dt for device outputs
@@ -147,6 +148,7 @@ int validate_launch(const fv_grid *g, const fv_launch *l, size_t smem_optin) {
     }
     if (k.tile[0] % 2) return FV_EINVAL;  // TMA boxes start on 16-byte boundaries
     if (k.threads < 32 || k.threads > 256 || k.threads % 32) return FV_EINVAL;
+    if (g->dim == 3 && !k.march && k.threads > kStage3dMaxThreads) return FV_EINVAL;
     if (k.grid != 0) return FV_EINVAL;  // tiled kernels cover the domain
     if (k.loader != FV_LOADER_TMA && k.loader != FV_LOADER_PLAIN) return FV_EINVAL;
     const size_t smem = k.march ? march_smem_bytes(k.tile) : stage_smem_bytes(g->dim, k.tile);
@@ -246,10 +248,19 @@ int dt_launch(fv_ctx *c, const double *U, cudaStream_t st) {
   for (int d = 0; d < 3; ++d) a.inv_h[d] = (d < c->grid.dim) ? c->grid.n[d] / c->grid.len[d] : 0.0;
   a.smax = c->smax;
   a.flags = c->flags;
+  // FP32 pre-selection where its error bound applies (1/dx within [2^-30, 2^30],
+  // 2^-20 <= gamma - 1 and gamma < 1e6: no FP32 overflow or underflow)
+  bool b = c->scheme.gamma < 1e6 && a.g1 >= 0x1p-20;
+  for (int d = 0; d < c->grid.dim; ++d) b = b && a.inv_h[d] >= 0x1p-30 && a.inv_h[d] <= 0x1p30;
+  a.bounded = b ? 1 : 0;
+  a.lbound = c->lbound;
+  a.g1f = (float)a.g1;
+  a.gammaf = (float)a.gamma;
+  for (int d = 0; d < 3; ++d) a.inv_hf[d] = (float)a.inv_h[d];
   int blocks = c->launch.dt.grid > 0 ? c->launch.dt.grid : 2 * c->sms;
   const long long need = (c->ncells + c->launch.dt.threads - 1) / c->launch.dt.threads;
   if (blocks > need) blocks = (int)(need > 0 ? need : 1);
-  FV_CK(cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long), st));
+  FV_CK(cudaMemsetAsync(c->smax, 0, 16, st));  // smax and the FP32 bound
   FV_CK(launch_dt(a, blocks, c->launch.dt.threads, st));
   return FV_OK;
 }
@@ -572,14 +583,15 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(FV_ECUDA);
   if (cudaMalloc(&c->U1, c->state_bytes) != cudaSuccess || cudaMalloc(&c->U2, c->state_bytes) != cudaSuccess)
     return fail(cuda_fail(cudaErrorMemoryAllocation));
-  // scratch: smax (8) | flags (8) | t_acc (8) | dt (8) | norms (8 * 5)
+  // scratch: smax (8) | FP32 lower bound (4) + pad | flags (8) | t_acc (8) | dt (8) | norms (8 * 5)
   char *scr = nullptr;
   if (cudaMalloc(&scr, 256) != cudaSuccess) return fail(cuda_fail(cudaErrorMemoryAllocation));
   c->smax = reinterpret_cast<unsigned long long *>(scr);
-  c->flags = reinterpret_cast<unsigned *>(scr + 8);
-  c->t_acc = reinterpret_cast<double *>(scr + 16);
-  c->dt_dev = reinterpret_cast<double *>(scr + 24);
-  c->norm_out = reinterpret_cast<double *>(scr + 32);
+  c->lbound = reinterpret_cast<unsigned *>(scr + 8);
+  c->flags = reinterpret_cast<unsigned *>(scr + 16);
+  c->t_acc = reinterpret_cast<double *>(scr + 24);
+  c->dt_dev = reinterpret_cast<double *>(scr + 32);
+  c->norm_out = reinterpret_cast<double *>(scr + 40);
   if (cudaMemset(scr, 0, 256) != cudaSuccess) return fail(FV_ECUDA);
   if ((r = set_attributes(c))) return fail(r);
   if (c->ngrids > 1 && (r = batch_setup(c))) return fail(r);

@@ -5,6 +5,9 @@
 
 namespace fvk {
 
+// Largest CTA of the 3D box-tiled stage kernel (its register budget).
+constexpr int kStage3dMaxThreads = 192;
+
 // Work of one launch of the fused stage kernel.
 enum StageMode : int {
   MODE_RESIDUAL = 0,  // out = R_h (Eq. (5), face areas included)
@@ -47,6 +50,12 @@ struct DtArgs {
   double inv_h[3];
   unsigned long long *smax;  // atomicMax target (bits of a non-negative double)
   unsigned *flags;
+  // FP32 pre-selection (bounded = 1): lbound receives the bits of the largest
+  // certified lower bound of a cell's wave-speed sum; the exact pass then
+  // evaluates in FP64 only the cells whose certified upper bound reaches it
+  int bounded;
+  unsigned *lbound;
+  float g1f, gammaf, inv_hf[3];
 };
 
 // One problem of a batched context (2D).

@@ -96,10 +96,11 @@ __device__ __forceinline__ void load_halo(double *tile, const StageArgs &a, cons
 // limiters are symmetric (Psi(r) = r Psi(1/r)), so the two kappa-weighted
 // limited slopes coincide and the states are q -+ eps/2 * slope; without a
 // limiter the kappa weights cL = eps(1-kappa)/4, cR = eps(1+kappa)/4 apply.
+// muscl_from_diffs takes the stencil's three differences dm = q1 - q0,
+// d0 = q2 - q1, dp = q3 - q2 (consecutive faces share two of them).
 template <int LIM>
-__device__ __forceinline__ void muscl_states(double q0, double q1, double q2, double q3, double h, double cL,
-                                             double cR, double &QL, double &QR) {
-  const double dm = q1 - q0, d0 = q2 - q1, dp = q3 - q2;
+__device__ __forceinline__ void muscl_from_diffs(double q1, double q2, double dm, double d0, double dp, double h,
+                                                 double cL, double cR, double &QL, double &QR) {
   if (LIM == FV_LIM_NONE) {
     QL = fma(cL, dm, fma(cR, d0, q1));
     QR = fma(-cR, d0, fma(-cL, dp, q2));
@@ -112,6 +113,12 @@ __device__ __forceinline__ void muscl_states(double q0, double q1, double q2, do
   }
 }
 
+template <int LIM>
+__device__ __forceinline__ void muscl_states(double q0, double q1, double q2, double q3, double h, double cL,
+                                             double cR, double &QL, double &QR) {
+  muscl_from_diffs<LIM>(q1, q2, q1 - q0, q2 - q1, q3 - q2, h, cL, cR, QL, QR);
+}
+
 template <int DIM, int D, int LIM>
 __device__ __forceinline__ void face_pass(const double *__restrict__ tile, double *__restrict__ F,
                                           double *__restrict__ R, const StageArgs &a, const int ext[3],
@@ -120,51 +127,85 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
   constexpr int NT = DIM - 1;
   constexpr int E = NV - 1;
   const int fe0 = ext[0] + (D == 0), fe1 = ext[1] + (D == 1), fe2 = (DIM == 3) ? ext[2] + (D == 2) : 1;
-  const int nf = fe0 * fe1 * fe2;
+  // Faces form lines along the normal axis D (fn faces each); a work item is a
+  // run of up to K consecutive faces of one line, so each face after the first
+  // takes one new stencil value and one new difference per variable.  Items
+  // are numbered with the line fastest (neighbouring threads, neighbouring
+  // lines); K = ceil(faces / threads) keeps one item per thread when the
+  // lines split evenly.
+  const int fn = (D == 0) ? fe0 : ((D == 1) ? fe1 : fe2);
+  const int la = (D == 0) ? fe1 : fe0;  // line index = a + la * b over the two other axes
+  const int nline = fe0 * fe1 * fe2 / fn;
+  const int K = (fn * nline + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int nrun = (fn + K - 1) / K;
   const int sstride = (D == 0) ? 1 : ((D == 1) ? G.BX : G.BX * G.BY);
+  const int fstr = (D == 0) ? 1 : ((D == 1) ? fe0 : fe0 * fe1);  // face-index stride along the normal
   const double h = a.half_eps;
-  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
-    const int i = f % fe0;
-    const int rr = f / fe0;
-    const int j = rr % fe1;
-    const int k = rr / fe1;
-    const int lx = (D == 0) ? i : i + 2;
-    const int ly = (D == 1) ? j : j + 2;
-    const int lz = (DIM == 3) ? ((D == 2) ? k : k + 2) : 0;
+  for (int item = threadIdx.x; item < nrun * nline; item += blockDim.x) {
+    const int run = item / nline, line = item - run * nline;
+    const int ca = line % la, cb = line / la;  // the line's two other-axis coordinates
+    const int m0 = run * K, m1 = min(m0 + K, fn);
+    int lx, ly, lz, f;  // box coordinates of stencil start of face m0, and its face index
+    if (D == 0) {
+      lx = m0, ly = ca + 2, lz = cb + 2;
+      f = (cb * fe1 + ca) * fe0 + m0;
+    } else if (D == 1) {
+      lx = ca + 2, ly = m0, lz = cb + 2;
+      f = (cb * fe1 + m0) * fe0 + ca;
+    } else {
+      lx = ca + 2, ly = cb + 2, lz = m0;
+      f = (m0 * fe1 + cb) * fe0 + ca;
+    }
+    if (DIM == 2) lz = 0;
     const double *p = tile + (lz * G.BY + ly) * G.BX + lx;
-    double QL[NV], QR[NV];
+    // carried from face to face: the two leading differences (stencil values
+    // are re-read from shared memory, which keeps the carried state small)
+    double dm[NV], d0[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double *pv = p + v * G.plane;
-      muscl_states<LIM>(pv[0], pv[sstride], pv[2 * sstride], pv[3 * sstride], h, a.cL, a.cR, QL[v], QR[v]);
+      dm[v] = pv[sstride] - pv[0];
+      d0[v] = pv[2 * sstride] - pv[sstride];
     }
-    // normal-first ordering: (rho, m_D, tangential momenta, E)
-    double qL[NT + 3], qR[NT + 3], Gf[NT + 3];
-    qL[0] = QL[0];
-    qR[0] = QR[0];
-    qL[1] = QL[1 + D];
-    qR[1] = QR[1 + D];
-    int t = 0;
+    for (int m = m0; m < m1; ++m, p += sstride, f += fstr) {
+      double QL[NV], QR[NV];
 #pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      if (ax == D) continue;
-      qL[2 + t] = QL[1 + ax];
-      qR[2 + t] = QR[1 + ax];
-      ++t;
-    }
-    qL[E] = QL[E];
-    qR[E] = QR[E];
-    roe_2F<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gf);
-    F[f] = Gf[0];
-    F[(1 + D) * G.fmax + f] = Gf[1];
-    t = 0;
+      for (int v = 0; v < NV; ++v) {
+        const double *pv = p + v * G.plane;
+        const double q1 = pv[sstride], q2 = pv[2 * sstride];
+        const double dp = pv[3 * sstride] - q2;
+        muscl_from_diffs<LIM>(q1, q2, dm[v], d0[v], dp, h, a.cL, a.cR, QL[v], QR[v]);
+        dm[v] = d0[v];
+        d0[v] = dp;
+      }
+      // normal-first ordering: (rho, m_D, tangential momenta, E)
+      double qL[NT + 3], qR[NT + 3], Gf[NT + 3];
+      qL[0] = QL[0];
+      qR[0] = QR[0];
+      qL[1] = QL[1 + D];
+      qR[1] = QR[1 + D];
+      int t = 0;
 #pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      if (ax == D) continue;
-      F[(1 + ax) * G.fmax + f] = Gf[2 + t];
-      ++t;
+      for (int ax = 0; ax < DIM; ++ax) {
+        if (ax == D) continue;
+        qL[2 + t] = QL[1 + ax];
+        qR[2 + t] = QR[1 + ax];
+        ++t;
+      }
+      qL[E] = QL[E];
+      qR[E] = QR[E];
+      roe_2F<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gf);
+      F[f] = Gf[0];
+      F[(1 + D) * G.fmax + f] = Gf[1];
+      t = 0;
+#pragma unroll
+      for (int ax = 0; ax < DIM; ++ax) {
+        if (ax == D) continue;
+        F[(1 + ax) * G.fmax + f] = Gf[2 + t];
+        ++t;
+      }
+      F[E * G.fmax + f] = Gf[E];
     }
-    F[E * G.fmax + f] = Gf[E];
   }
   __syncthreads();
   const int ncell = ext[0] * ext[1] * ((DIM == 3) ? ext[2] : 1);
@@ -328,13 +369,16 @@ __device__ __forceinline__ double *aligned_smem(unsigned char *raw) {
 }
 
 // One CTA per tile of the grid.  Register budget: FV_STAGE_MIN_BLOCKS resident
-// 256-thread CTAs per SM (2 by default: up to 128 registers per thread, no
-// spills; the default tiles' shared memory also allows two CTAs per SM).
+// CTAs of the largest allowed size per SM (2 by default; the default tiles'
+// shared memory also allows two CTAs per SM).  2D CTAs have up to 256
+// threads (up to 128 registers per thread, no spills); 3D CTAs up to 192,
+// which leaves 168 registers for the five-variable face runs (256 would spill).
 #ifndef FV_STAGE_MIN_BLOCKS
 #define FV_STAGE_MIN_BLOCKS 2
 #endif
 template <int DIM, int MODE, int LIM>
-__global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
+__global__ void __launch_bounds__(DIM == 2 ? 256 : kStage3dMaxThreads, FV_STAGE_MIN_BLOCKS)
+    stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
   constexpr int NV = DIM + 2;
   extern __shared__ unsigned char smem_raw[];
   __shared__ double s_coef[4];

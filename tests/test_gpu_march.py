@@ -28,7 +28,7 @@ def launch(g, tile, threads=256, loader=fv.FV_LOADER_TMA, march=1):
     return d
 
 
-BOX = ((16, 8, 4), 256)
+BOX = ((16, 8, 4), 192)
 
 
 def _grid(n, lens, bc, seed):
@@ -123,7 +123,7 @@ def test_march_launch_validation():
     g2, _ = I.isentropic_vortex(32)
     bad = [(g2, dict(tile=(16, 16, 1), march=1)), (g3, dict(tile=(16, 15, 4), march=2)),
            (g3, dict(tile=(16, 15, 0), march=1)), (g3, dict(tile=(15, 16, 4), march=1)),
-           (g3, dict(tile=(252, 252, 4), march=1))]
+           (g3, dict(tile=(252, 252, 4), march=1)), (g3, dict(tile=(8, 8, 8), threads=224, march=0))]
     for g, b in bad:
         d = fv.launch_to_dict(fv.fv_default_launch(g))
         for s_ in range(3):

@@ -84,12 +84,13 @@ def dev(U):
     return torch.from_numpy(np.ascontiguousarray(U)).cuda()
 
 
-def launch_with(g, tile=None, threads=256, loader=fv.FV_LOADER_TMA):
+def launch_with(g, tile=None, threads=None, loader=fv.FV_LOADER_TMA):
     d = fv.launch_to_dict(fv.fv_default_launch(g))
     for s in range(3):
         if tile is not None:
             d["stage"][s]["tile"] = tile
-        d["stage"][s]["threads"] = threads
+        if threads is not None:
+            d["stage"][s]["threads"] = threads
         d["stage"][s]["loader"] = loader
     return d
 
@@ -223,7 +224,7 @@ def test_launch_configuration_does_not_change_results(dim):
                 ((128, 2, 1), 256)]
     else:
         g, U = I.taylor_green(20, seed=2)
-        cfgs = [((16, 8, 4), 256), ((8, 8, 8), 128), ((4, 4, 2), 32), ((20, 4, 2), 160)]
+        cfgs = [((16, 8, 4), 192), ((8, 8, 8), 128), ((4, 4, 2), 32), ((20, 4, 2), 160)]
     outs = []
     for tile, thr in cfgs:
         for loader in (fv.FV_LOADER_TMA, fv.FV_LOADER_PLAIN):
