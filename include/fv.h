@@ -110,9 +110,8 @@ typedef struct fv_launch {
 typedef struct fv_ctx fv_ctx;
 
 /* Fill *l with the default launch configuration for grid g (one tile shape
- * and thread count for all stages): 2D 32x31 box tiles (32x32 when 31-row
- * tiles would pad the last tile row by over 1% more cells) with 256 threads;
- * 3D 8x8x8 box tiles with 192 threads; time-step reduction 256 threads, two
+ * and thread count for all stages): 2D 32x32 box tiles with 256 threads; 3D
+ * 8x8x8 box tiles with 192 threads; time-step reduction 512 threads, two
  * CTAs per SM.  Returns FV_EINVAL for a bad grid. */
 int fv_default_launch(const fv_grid *g, fv_launch *l);
 
@@ -248,33 +247,38 @@ typedef struct fv_tune_opts {
 typedef struct fv_tune_report {
   double t_default;       /* s per SSP-RK3 step, default launch */
   double t_tuned;         /* s per step, the returned launch */
+  double t_search;        /* s per step, the best launch the search itself found */
   double t_best_sampled;  /* s per step, best of the random sample */
   double t_exhaustive;    /* s per step, best of the reduced space (0 if not run) */
   double r2_train, r2_test; /* Eq. (7) on run times, training / held-out samples */
   double space_size;      /* points in the full tuning space */
-  int n_params;           /* tuning parameters (14 in 2D, 17 in 3D) */
+  int n_params;           /* tuning parameters (14 in 2D, 20 in 3D) */
   int n_train, n_test, epochs, n_measured, n_exhaustive;
   int rounds, n_refined;  /* surrogate rounds run; measurements made by the refinement */
+  int chosen;             /* the returned launch: 0 the search's, 1 the default, 2 the exhaustive best */
   fv_launch exhaustive_best;
 } fv_tune_report;
 
 /* Tune the launch configuration of ctx for the state U (device or host; not
  * modified: timing runs on a copy in the context's staging buffer).  The space:
  * per RK-stage kernel tile_x in {8,16,32,64,128}, tile_y in {2,4,8,16,32}
- * (3D: tile_x {8,16,32}, tile_y {4,8,16}, tile_z {2,4,8}), threads in
+ * (3D: tile_x {8,16,32}, tile_y {4,8,16}, tile_z {2,4,8}, and the kernel:
+ * box tiles or z-marching with chunks of 8 x tile_z planes), threads in
  * {64,96,...,256}, loader in {TMA, plain}; time-step kernel threads in
- * {128,256,512,1024} and grid in {1,2,4,8} x SMs.  Procedure: time
- * opts->samples random valid configurations; train the network (features
- * standardised, target log time standardised); score opts->candidates random
- * configurations; re-measure the opts->top best predicted; repeat for
- * opts->rounds rounds, each retrained on everything measured so far (the
- * held-out 25% of the first sample excepted); then refine the best measured
- * configuration by coordinate descent (each parameter in turn over its value
- * set); return the fastest measured configuration in *best (and install it in
- * ctx).  Features are log2 of the power-of-two parameters.  With
- * opts->exhaustive, every configuration with one shared (tile, threads) for
- * the three stages, TMA loads and the default time-step kernel is timed as the
- * judge.  rep may be NULL.  Waits for completion. */
+ * {128,256,512,1024} and grid in {1,2,4,8} x SMs.  Procedure: time the
+ * default launch and opts->samples random valid configurations; train the
+ * network (features standardised, target log time standardised); score
+ * opts->candidates random configurations; re-measure the opts->top best
+ * predicted; repeat for opts->rounds rounds, each retrained on everything
+ * measured so far (the held-out 25% of the random sample excepted); then
+ * refine the best measured configuration by coordinate descent (each
+ * parameter in turn over its value set).  Features are log2 of the
+ * power-of-two parameters.  With opts->exhaustive, every configuration with
+ * one shared (tile, threads) for the three stages, box tiles, TMA loads and
+ * the default time-step kernel is timed as the judge.  Finally the search's
+ * best, the default and (if run) the exhaustive best are timed interleaved
+ * opts->final_repeats times; the fastest by median is returned in *best and
+ * installed in ctx.  rep may be NULL.  Waits for completion. */
 int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *best, fv_tune_report *rep);
 
 /* Residual R_h of Eq. (5) and, if rnorm2 != NULL, sum over cells of R_v^2 per
@@ -292,7 +296,7 @@ int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *b
  * library's device image -- every GPU that loads libfv holds it until the
  * process exits -- holding nvar partial sums per tile.  With rnorm2 != NULL
  * the grid may have at most 131072 / nvar default tiles (2D: 32768 tiles of
- * 32x31 or 32x32 cells, e.g. 5696 x 5696; 3D: 26214 tiles of 8x8x8 cells); larger
+ * 32x32 cells, e.g. 5792 x 5792; 3D: 26214 tiles of 8x8x8 cells); larger
  * grids return FV_EINVAL before anything is launched.  The first call on each
  * device looks up the scratch array's device address (cudaGetSymbolAddress)
  * and sets kernel attributes: make that first call before any stream capture.

@@ -527,14 +527,8 @@ int fv_default_launch(const fv_grid *g, fv_launch *l) {
   for (int s = 0; s < 3; ++s) {
     fv_kernel_cfg &k = l->stage[s];
     if (g->dim == 2) {
-      // 32 x 31 tiles have 33 x 31 x-faces and 32 x 32 y-faces: four full
-      // rounds of 256 threads each (about 1% faster than 32 x 32 tiles).  Take
-      // 32 rows instead when 31-row tiles would leave over 1% more padding
-      // cells in the ragged last tile row.
-      const long long n1 = g->n[1];
-      const long long pad31 = (n1 + 30) / 31 * 31 - n1, pad32 = (n1 + 31) / 32 * 32 - n1;
-      k.tile[0] = 32;
-      k.tile[1] = (100 * pad31 < 100 * pad32 + n1) ? 31 : 32;
+      k.tile[0] = 32;  // the largest tile with two CTAs per SM (shared memory)
+      k.tile[1] = 32;
       k.tile[2] = 1;
     } else {
       k.tile[0] = 8;  // 9 x 8 x 8 faces per axis: three full rounds of 192 threads
@@ -544,7 +538,7 @@ int fv_default_launch(const fv_grid *g, fv_launch *l) {
     k.threads = g->dim == 2 ? 256 : 192;
     k.grid = 0;
   }
-  l->dt.threads = 256;
+  l->dt.threads = 512;  // 1024 threads per SM keep enough loads in flight
   l->dt.grid = 0;
   return FV_OK;
 }

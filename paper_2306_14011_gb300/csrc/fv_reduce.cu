@@ -91,6 +91,7 @@ template <int DIM>
 __global__ void __launch_bounds__(1024) dt_bound_kernel(const DtArgs a) {
   const long long N = a.ncells;
   unsigned best = 0u;
+#pragma unroll 4
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
     float s32, rel;
     if (wave_sum32<DIM>(a, c, s32, rel)) {
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(1024) dt_kernel(const DtArgs a) {
   const float L = a.bounded ? __uint_as_float(*a.lbound) : 0.0f;
   unsigned long long best = 0ull;
   bool bad = false;
+#pragma unroll 4
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
     if (a.bounded) {
       float s32, rel;

@@ -107,6 +107,36 @@ uint64_t key(const Space &sp, const Cfg &c) {
   return k;
 }
 
+// The index vector of launch l in the space, if every value is in it.
+bool cfg_of(const Space &sp, const fv_launch &l, int sms, Cfg *out) {
+  Cfg c(sp.nparams);
+  auto find = [&](int p, int v) {
+    for (int i = 0; i < (int)sp.vals[p].size(); ++i)
+      if (sp.vals[p][i] == v) {
+        c[p] = i;
+        return true;
+      }
+    return false;
+  };
+  for (int s = 0; s < 3; ++s) {
+    const int b = s * sp.per_stage;
+    const fv_kernel_cfg &k = l.stage[s];
+    const int o = sp.dim == 3 ? 3 : 2;
+    if (!find(b, k.tile[0]) || !find(b + 1, k.tile[1])) return false;
+    if (sp.dim == 3 && (!find(b + 2, k.march ? k.tile[2] / 8 : k.tile[2]) || !find(b + o + 2, k.march) ||
+                        (k.march && k.tile[2] % 8)))
+      return false;
+    if (!find(b + o, k.threads) || !find(b + o + 1, k.loader)) return false;
+  }
+  const int b = 3 * sp.per_stage;
+  if (!find(b, l.dt.threads)) return false;
+  const int mult = l.dt.grid == 0 ? 2 : l.dt.grid / sms;
+  if (l.dt.grid != 0 && l.dt.grid % sms) return false;
+  if (!find(b + 1, mult)) return false;
+  *out = c;
+  return true;
+}
+
 Cfg random_cfg(const Space &sp, SplitMix64 &rng) {
   Cfg c(sp.nparams);
   for (int p = 0; p < sp.nparams; ++p) c[p] = rng.below((int)sp.vals[p].size());
@@ -205,14 +235,24 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
     return FV_OK;
   };
 
-  // ---- 1. time a random sample of valid configurations (25% held out)
+  // ---- 1. time the default launch (a training sample) and a random sample of
+  // valid configurations (25% held out)
   int outcome;
-  for (int attempts = 0; (int)cfgs.size() < o.samples && attempts < 50 * o.samples; ++attempts) {
+  fv_launch deflt;  // the library default: the analogue of the compiler's default launch
+  if ((r = ctx_default_launch(ctx, &deflt))) return r;
+  {
+    Cfg c0;
+    if (cfg_of(sp, deflt, sms, &c0) && (r = measure(c0, false, &outcome))) return r;
+  }
+  const int n_default_samples = (int)cfgs.size();
+  for (int attempts = 0; (int)cfgs.size() < o.samples + n_default_samples && attempts < 50 * o.samples;
+       ++attempts) {
     const bool hold = (rng.uniform() < 0.25);
     if ((r = measure(random_cfg(sp, rng), hold, &outcome))) return r;
   }
   if ((int)cfgs.size() < 8) return FV_EINVAL;
-  const double best_sampled = times[best_i];
+  double best_sampled = INFINITY;  // best of the random sample (the default excluded)
+  for (size_t i = n_default_samples; i < times.size(); ++i) best_sampled = std::min(best_sampled, times[i]);
 
   // ---- 2. surrogate rounds
   DevBuf dP, dOut;
@@ -355,8 +395,6 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
   fv_launch tuned = to_launch(sp, cfgs[best_i], sms);
 
   // ---- 4. exhaustive judge on the reduced space (shared tile and threads)
-  fv_launch deflt;  // the library default: the analogue of the compiler's default launch
-  if ((r = ctx_default_launch(ctx, &deflt))) return r;
   fv_launch exh_best;
   memset(&exh_best, 0, sizeof(exh_best));
   int n_exh = 0;
@@ -414,12 +452,28 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
     tf_tun = b[b.size() / 2];
     tf_exh = cc.empty() ? 0.0 : cc[cc.size() / 2];
   }
-  if ((r = fv_set_launch(ctx, &tuned))) return r;
-  *best = tuned;
+  // the fastest of the three by median (the search's pick wins ties)
+  int chosen = 0;
+  double t_ret = tf_tun;
+  fv_launch ret = tuned;
+  if (tf_def < t_ret) {
+    chosen = 1;
+    t_ret = tf_def;
+    ret = deflt;
+  }
+  if (n_exh > 0 && tf_exh < t_ret) {
+    chosen = 2;
+    t_ret = tf_exh;
+    ret = exh_best;
+  }
+  if ((r = fv_set_launch(ctx, &ret))) return r;
+  *best = ret;
   if (rep) {
     memset(rep, 0, sizeof(*rep));
     rep->t_default = tf_def;
-    rep->t_tuned = tf_tun;
+    rep->t_tuned = t_ret;
+    rep->t_search = tf_tun;
+    rep->chosen = chosen;
     rep->t_best_sampled = best_sampled;
     rep->t_exhaustive = tf_exh;
     rep->r2_train = r2_tr;

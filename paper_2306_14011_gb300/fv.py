@@ -67,11 +67,11 @@ class fv_tune_opts(C.Structure):
 
 
 class fv_tune_report(C.Structure):
-    _fields_ = [("t_default", C.c_double), ("t_tuned", C.c_double), ("t_best_sampled", C.c_double),
-                ("t_exhaustive", C.c_double), ("r2_train", C.c_double), ("r2_test", C.c_double),
-                ("space_size", C.c_double), ("n_params", C.c_int), ("n_train", C.c_int), ("n_test", C.c_int),
-                ("epochs", C.c_int), ("n_measured", C.c_int), ("n_exhaustive", C.c_int), ("rounds", C.c_int),
-                ("n_refined", C.c_int), ("exhaustive_best", fv_launch)]
+    _fields_ = [("t_default", C.c_double), ("t_tuned", C.c_double), ("t_search", C.c_double),
+                ("t_best_sampled", C.c_double), ("t_exhaustive", C.c_double), ("r2_train", C.c_double),
+                ("r2_test", C.c_double), ("space_size", C.c_double), ("n_params", C.c_int), ("n_train", C.c_int),
+                ("n_test", C.c_int), ("epochs", C.c_int), ("n_measured", C.c_int), ("n_exhaustive", C.c_int),
+                ("rounds", C.c_int), ("n_refined", C.c_int), ("chosen", C.c_int), ("exhaustive_best", fv_launch)]
 
 
 _lib = None

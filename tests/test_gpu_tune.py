@@ -84,6 +84,26 @@ def test_tuner_beats_default_and_matches_exhaustive_judge():
         assert torch.equal(s.residual(Ud), R_default)
         # the surrogate predicts held-out configurations better than their mean does
         assert rep["r2_test"] > 0.0
-        # tuned is at least as fast as the default and as the exhaustive judge (3% timing noise)
-        assert rep["t_tuned"] <= rep["t_default"] * 1.03
-        assert rep["t_tuned"] <= rep["t_exhaustive"] * 1.03
+        # the returned launch is the fastest of the search's pick, the default and
+        # the exhaustive judge; the search alone (which starts from the default)
+        # is within 3% timing noise of both
+        assert rep["t_tuned"] <= min(rep["t_default"], rep["t_search"])
+        assert rep["chosen"] in (0, 1, 2)
+        assert rep["t_search"] <= rep["t_default"] * 1.03
+        assert rep["t_search"] <= rep["t_exhaustive"] * 1.03
+
+
+def test_tuner_3d_space_includes_the_marching_kernel():
+    """A short 3D search: 20 parameters (box or z-marching per stage); the
+    installed launch changes speed only."""
+    g, U = I.taylor_green(48, seed=2)
+    Ud = torch.from_numpy(U).cuda()
+    with fv.Solver(g) as s:
+        R_default = s.residual(Ud).clone()
+        best, rep = s.tune(Ud, samples=40, candidates=20000, top=8, rounds=1, refine=1, exhaustive=0, steps=2,
+                           final_repeats=3, seed=3)
+        assert rep["n_params"] == 20
+        assert rep["space_size"] == float((3 * 3 * 3 * 7 * 2 * 2) ** 3 * 4 * 4)
+        assert s.launch == best
+        assert rep["t_tuned"] <= rep["t_default"]
+        assert torch.equal(s.residual(Ud), R_default)
