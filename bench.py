@@ -51,9 +51,9 @@ BYTES_PER_CELL_STAGE_3D = 320.0 / 3.0
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one stage-kernel launch from ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, full 4096^2 launches, mean of the three stages of one
-# step), valid for the kernel sources whose hash is recorded with it; null
-# otherwise.
-STAGE_TRAFFIC = {"bytes": 1.3913e9, "source_hash": "f1100ee232bd7c88"}
+# step), valid for the kernel sources whose hash and the launch shape recorded
+# with it; null otherwise.
+STAGE_TRAFFIC = {"bytes": 1.3912e9, "source_hash": "f1100ee232bd7c88", "tile": [32, 32, 1], "threads": 256}
 
 
 def kernel_source_hash() -> str:
@@ -239,7 +239,10 @@ def run_ours(args):
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     achieved_gbs = W["bytes"] * cells / (stage_ms / 1e3) / 1e9
-    traffic = STAGE_TRAFFIC["bytes"] if STAGE_TRAFFIC["source_hash"] == kernel_source_hash() else None
+    st0 = solver.launch["stage"][0]
+    traffic = STAGE_TRAFFIC["bytes"] if (STAGE_TRAFFIC["source_hash"] == kernel_source_hash() and
+                                         list(st0["tile"]) == STAGE_TRAFFIC["tile"] and
+                                         st0["threads"] == STAGE_TRAFFIC["threads"]) else None
     line = {
         "metric": METRIC,
         "value": value,
@@ -425,6 +428,110 @@ def run_reference(args):
     }
 
 
+def run_adjoint(args):
+    """Discrete-adjoint workload: the gradient of the kinetic energy after 400
+    fixed-dt SSP-RK3 steps of the 1024^2 periodic isentropic vortex with
+    respect to the initial state, through FvRunFunction with checkpoints every
+    20 steps (forward with checkpoints; per segment, recompute and 20 RK-step
+    VJPs).  One bench step = one whole gradient; value = differentiated
+    cell-stages per second (cells x 3 x 400 / gradient time).  Also times one
+    residual VJP, one RK-step VJP and one RK step alone (CUDA events)."""
+    import torch
+
+    from paper_2306_14011_gb300 import fv
+    from paper_2306_14011_gb300 import inputs as I
+    from paper_2306_14011_gb300.autograd import FvRunFunction, kinetic_energy
+
+    dist, rank, world = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    n, nsteps, every = (args.n if args.n != N_CELLS_SIDE else 1024), 400, 20
+    g, U0 = I.isentropic_vortex(n, noise=0.0)
+    solver = fv.Solver(g, stream=stream)
+    Ud = torch.from_numpy(U0).to(dev)
+    dt = solver.time_step(Ud)
+
+    def gradient():
+        X = Ud.clone().requires_grad_()
+        kinetic_energy(FvRunFunction.apply(X, solver, nsteps, dt, every), g).backward()
+        return X.grad
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        gradient()
+    barrier()
+    clocks = ClockSampler(gpu_uuid(torch))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        gradient()
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    solver.sync()
+
+    def timed(f, reps=10):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            f()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    lam = torch.randn_like(Ud)
+    out = torch.empty_like(Ud)
+    R = torch.empty_like(Ud)
+    X = Ud.clone()
+    t_res = timed(lambda: solver.residual(Ud, R))
+    t_rvjp = timed(lambda: solver.residual_vjp(Ud, lam, out))
+    t_step = timed(lambda: solver.rk_step(X, dt))
+    t_svjp = timed(lambda: solver.rk_step_vjp(Ud, lam, dt, out))
+    solver.close()
+    if rank != 0:
+        return None
+    cells = g.ncells
+    # kernels per gradient: forward 400 x 3 stage launches; backward, per
+    # segment, 19 recomputed steps x 3 and 20 RK-step VJPs x (2 stage
+    # recomputations + 3 adjoint launches)
+    launches = nsteps * 3 + (nsteps // every) * ((every - 1) * 3 + every * 5)
+    return {
+        "metric": f"differentiated FP64 cell-stages/s (gradient of the kinetic energy after {nsteps} SSP-RK3 steps, "
+                  f"2D Euler vortex {n}^2, checkpoints every {every})",
+        "value": whole_job_rate(cells * 3 * nsteps * args.steps, world, ms / 1e3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (isentropic vortex initial condition)",
+        "config": {"workload": f"gradient of J = kinetic energy after {nsteps} fixed-dt SSP-RK3 steps of the {n}x{n} "
+                               f"periodic isentropic vortex w.r.t. U0; FvRunFunction, checkpoints every {every}; "
+                               "1 bench step = 1 gradient", "cells": cells, "launch": "default",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": None,
+        "adjoint": {"residual_ms": t_res, "residual_vjp_ms": t_rvjp, "rk_step_ms": t_step, "rk_step_vjp_ms": t_svjp,
+                    "vjp_over_residual": t_rvjp / t_res, "step_vjp_over_step": t_svjp / t_step,
+                    "gradient_over_forward_run": (ms / args.steps) / (nsteps * t_step)},
+        "e2e": None,
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+        "impl": "ours",
+    }
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -432,9 +539,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=N_CELLS_SIDE, help="grid cells per side (default: the workload's 4096)")
-    ap.add_argument("--workload", choices=("kh4096", "tgv384", "sod96"), default="kh4096",
+    ap.add_argument("--workload", choices=("kh4096", "tgv384", "sod96", "adjoint1024"), default="kh4096",
                     help="kh4096: the metric's configuration (default); tgv384: 3D Taylor-Green; "
-                         "sod96: 96 batched Sod grids")
+                         "sod96: 96 batched Sod grids; adjoint1024: gradient through 400 steps (one bench step "
+                         "= one gradient)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-rows", type=int, default=1024)
@@ -444,7 +552,12 @@ def main():
     ap.add_argument("--tune-samples", type=int, default=300)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.workload == "adjoint1024":
+        line = run_adjoint(args)
+    else:
+        line = run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -281,6 +281,13 @@ typedef struct fv_tune_report {
  * installed in ctx.  rep may be NULL.  Waits for completion. */
 int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *best, fv_tune_report *rep);
 
+/* The autotuner's search space for a dim-dimensional grid: *n_params tuning
+ * parameters and *size points (the product of the value-set sizes listed at
+ * fv_tune; the paper's analogue, Sec. 3.4, is 14 parameters over 10^7 x 12^7
+ * points).  Host only: needs no GPU.  Returns FV_EINVAL unless dim is 2 or 3
+ * and both pointers are non-NULL. */
+int fv_tune_space(int dim, int *n_params, double *size);
+
 /* Residual R_h of Eq. (5) and, if rnorm2 != NULL, sum over cells of R_v^2 per
  * variable -- the same values as fv_residual -- without a context and without
  * allocating anything.  The paper has no counterpart: this is a facility for

@@ -167,6 +167,16 @@ struct DevBuf {
 
 }  // namespace
 
+extern "C" int fv_tune_space(int dim, int *n_params, double *size) {
+  if ((dim != 2 && dim != 3) || !n_params || !size) return FV_EINVAL;
+  const Space sp = make_space(dim);
+  double points = 1.0;
+  for (auto &v : sp.vals) points *= (double)v.size();
+  *n_params = sp.nparams;
+  *size = points;
+  return FV_OK;
+}
+
 extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in, fv_launch *best,
                        fv_tune_report *rep) {
   if (!ctx || !U || !best) return FV_EINVAL;

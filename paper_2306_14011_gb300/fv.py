@@ -108,6 +108,8 @@ def load() -> C.CDLL:
         L.fv_mlp_predict.restype = C.c_int
         L.fv_tune.argtypes = [_VP, _VP, P(fv_tune_opts), P(fv_launch), P(fv_tune_report)]
         L.fv_tune.restype = C.c_int
+        L.fv_tune_space.argtypes = [C.c_int, P(C.c_int), P(C.c_double)]
+        L.fv_tune_space.restype = C.c_int
         L.fv_layout.argtypes = [_VP, P(C.c_longlong), C.c_int]
         L.fv_layout.restype = C.c_int
         L.fv_adjoint_vjp.argtypes = [_VP, C.c_int, _VP, _VP, C.c_double, _VP]
@@ -326,6 +328,14 @@ def fv_tune(ctx: int, U, **opts):
     report = {f[0]: getattr(rep, f[0]) for f in fv_tune_report._fields_ if f[0] != "exhaustive_best"}
     report["exhaustive_best"] = launch_to_dict(rep.exhaustive_best) if rep.n_exhaustive else None
     return launch_to_dict(best), report
+
+
+def fv_tune_space(dim: int):
+    """(number of tuning parameters, points in the search space) for a dim-D grid."""
+    n = C.c_int(0)
+    size = C.c_double(0.0)
+    _check(load().fv_tune_space(dim, C.byref(n), C.byref(size)), "fv_tune_space")
+    return n.value, size.value
 
 
 FV_VJP_RESIDUAL, FV_VJP_RKSTEP = 0, 1

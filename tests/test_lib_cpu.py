@@ -82,3 +82,17 @@ def test_init_without_a_gpu_reports_an_error_not_a_crash():
     st = lib.fv_init(C.byref(ctx), C.byref(G), 1, C.byref(S), None, None)
     assert st in (fv.FV_ECUDA, fv.FV_ENOMEM)
     assert not ctx.value
+
+
+def test_tuning_space_sizes():
+    """The tuner's space, and the paper's Table space (Sec. 3.4: 7 kernels with
+    gang 100, 200, ..., 1000 and vector length 32, 64, ..., 384 each) counted
+    the same way: the paper states 10^7 x 12^7 = 3.58e14 points."""
+    assert fv.fv_tune_space(2) == (14, float((5 * 5 * 7 * 2) ** 3 * 4 * 4))
+    assert fv.fv_tune_space(3) == (20, float((3 * 3 * 3 * 7 * 2 * 2) ** 3 * 4 * 4))
+    gang, vector = range(100, 1001, 100), range(32, 385, 32)
+    assert (len(gang), len(vector)) == (10, 12)
+    paper_points = len(gang) ** 7 * len(vector) ** 7
+    assert paper_points == 10 ** 7 * 12 ** 7 and f"{paper_points:.2e}" == "3.58e+14"
+    with pytest.raises(fv.FvError):
+        fv.fv_tune_space(4)
