@@ -8,7 +8,9 @@ state every `every` steps; the backward pass re-runs each segment from its
 checkpoint, keeping that segment's step states, then reverses it.  Forward
 work is about doubled; stored states are nsteps/every + every.
 
-FvResidualFunction.apply(U, solver) is R_h(U) (Eq. (5)) with its VJP.
+FvResidualFunction.apply(U, solver) is R_h(U) (Eq. (5)) with its VJP, and
+FvStepFunction.apply(U, solver, dt) one SSP-RK3 step with the step held at dt
+(Eq. (4)) with its VJP, for composing steps with other torch operations.
 Everything runs in the library's kernels; torch only holds the tensors.
 """
 from __future__ import annotations
@@ -29,6 +31,23 @@ class FvResidualFunction(torch.autograd.Function):
     def backward(ctx, gR):
         (U,) = ctx.saved_tensors
         return ctx.solver.residual_vjp(U.detach().contiguous(), gR.contiguous()), None
+
+
+class FvStepFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, solver, dt: float):
+        if not dt > 0.0:
+            raise ValueError("a differentiated step needs a fixed step dt > 0")
+        ctx.solver, ctx.dt = solver, dt
+        ctx.save_for_backward(U)
+        X = U.detach().contiguous().clone()
+        solver.rk_step(X, dt)
+        return X
+
+    @staticmethod
+    def backward(ctx, gU):
+        (U,) = ctx.saved_tensors
+        return ctx.solver.rk_step_vjp(U.detach().contiguous(), gU.contiguous(), ctx.dt), None, None
 
 
 class FvRunFunction(torch.autograd.Function):

@@ -96,7 +96,7 @@ struct fv_ctx {
   std::vector<long long> offsets;  // ngrids + 1, in doubles
   BatchProblem *b_prob;
   int *b_tile_begin, *b_chunk_begin;
-  unsigned long long *b_smax;      // [2][ngrids]
+  unsigned long long *b_smax;      // [2][ngrids], then the FP32 lower bounds [2][ngrids]
   double *b_tacc;                  // [ngrids]
   unsigned *b_bar;                 // count, generation
   int b_total_tiles, b_total_chunks, b_blocks;
@@ -346,7 +346,11 @@ int batch_setup(fv_ctx *c) {
       const double h = G.len[d] / G.n[d];
       p.half_inv_h[d] = 0.5 / h;
       p.inv_h[d] = G.n[d] / G.len[d];
+      p.inv_hf[d] = (float)p.inv_h[d];
     }
+    // the FP32 pre-selection's conditions (as for single grids)
+    p.bounded = c->scheme.gamma < 1e6 && c->scheme.gamma - 1.0 >= 0x1p-20 && p.inv_h[0] >= 0x1p-30 &&
+                p.inv_h[0] <= 0x1p30 && p.inv_h[1] >= 0x1p-30 && p.inv_h[1] <= 0x1p30;
     p.half_inv_h[2] = 0.5;
     for (int d = 0; d < 3; ++d) {
       p.bc[d][0] = G.bc[d][0];
@@ -388,7 +392,7 @@ int batch_init(fv_ctx *c, const fv_grid *grids, int ngrids) {
   FV_CK(cudaMalloc(&c->b_prob, sizeof(BatchProblem) * ngrids));
   FV_CK(cudaMalloc(&c->b_tile_begin, sizeof(int) * (ngrids + 1)));
   FV_CK(cudaMalloc(&c->b_chunk_begin, sizeof(int) * (ngrids + 1)));
-  FV_CK(cudaMalloc(&c->b_smax, sizeof(unsigned long long) * 2 * ngrids));
+  FV_CK(cudaMalloc(&c->b_smax, (sizeof(unsigned long long) + sizeof(unsigned)) * 2 * ngrids));
   FV_CK(cudaMalloc(&c->b_tacc, sizeof(double) * ngrids));
   FV_CK(cudaMalloc(&c->b_bar, sizeof(unsigned) * 2));
   FV_CK(cudaMemset(c->b_bar, 0, sizeof(unsigned) * 2));
@@ -421,6 +425,9 @@ int batch_run(fv_ctx *c, double *Ud, int nsteps, double dt_fixed, bool want_t) {
     b.U1 = c->U1;
     b.U2 = c->U2;
     b.smax = c->b_smax;
+    b.lbound = reinterpret_cast<unsigned *>(c->b_smax + 2 * c->ngrids);
+    b.g1f = (float)(c->scheme.gamma - 1.0);
+    b.gammaf = (float)c->scheme.gamma;
     b.t_acc = c->b_tacc;
     b.flags = c->flags;
     b.bar_count = c->b_bar;
@@ -435,7 +442,7 @@ int batch_run(fv_ctx *c, double *Ud, int nsteps, double dt_fixed, bool want_t) {
     const int blocks = c->b_blocks < c->b_total_tiles ? c->b_blocks : c->b_total_tiles;
     cudaGraph_t graph;
     FV_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(c->b_smax, 0, sizeof(unsigned long long) * 2 * n, c->cap);
+    cudaError_t e = cudaMemsetAsync(c->b_smax, 0, (sizeof(unsigned long long) + sizeof(unsigned)) * 2 * n, c->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->b_tacc, 0, sizeof(double) * n, c->cap);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->b_bar, 0, sizeof(unsigned), c->cap);
     if (e == cudaSuccess)

@@ -111,7 +111,42 @@ __device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double
   return grid_barrier(b.bar_count, b.bar_gen, b.flags);
 }
 
-// Per problem max over its cells of sum_d (|u_d| + c) / dx_d (as in dt_kernel).
+// Per problem, the largest certified FP32 lower bound of the wave-speed sum
+// (as in dt_bound_kernel), for problems where the pre-selection applies.
+__device__ __forceinline__ void dt_bound_phase(const BatchArgs &b, int slot) {
+  __shared__ unsigned wmax[32];
+  for (int item = blockIdx.x; item < b.total_chunks; item += gridDim.x) {
+    const int p = find_problem(b.chunk_begin, b.nprob, item);
+    const BatchProblem &P = b.prob[p];
+    if (!P.bounded) continue;  // uniform over the CTA
+    const long long N = (long long)P.n[0] * P.n[1];
+    const long long c0 = (long long)(item - b.chunk_begin[p]) * b.chunk_cells;
+    const long long c1 = c0 + b.chunk_cells < N ? c0 + b.chunk_cells : N;
+    const double *U = b.U + P.off;
+    unsigned best = 0u;
+    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      float s32, rel;
+      if (wave_sum32<2>(U, N, c, b.g1f, b.gammaf, P.inv_hf, s32, rel)) {
+        const unsigned lo = __float_as_uint(__fmul_rd(s32, __fsub_rd(1.0f, rel)));
+        best = lo > best ? lo : best;
+      }
+    }
+    best = __reduce_max_sync(0xffffffffu, best);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wmax[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = (blockDim.x + 31) >> 5;
+      const unsigned m = __reduce_max_sync(0xffffffffu, lane < nw ? wmax[lane] : 0u);
+      if (lane == 0) atomicMax(b.lbound + (long long)slot * b.nprob + p, m);
+    }
+    __syncthreads();
+  }
+}
+
+// Per problem max over its cells of sum_d (|u_d| + c) / dx_d (as in dt_kernel:
+// cells whose certified FP32 upper bound is below the problem's lower bound
+// are skipped, every other cell is evaluated in FP64).
 __device__ __forceinline__ void dt_phase(const BatchArgs &b, int slot) {
   __shared__ unsigned long long wmax[32];
   for (int item = blockIdx.x; item < b.total_chunks; item += gridDim.x) {
@@ -121,9 +156,16 @@ __device__ __forceinline__ void dt_phase(const BatchArgs &b, int slot) {
     const long long c0 = (long long)(item - b.chunk_begin[p]) * b.chunk_cells;
     const long long c1 = c0 + b.chunk_cells < N ? c0 + b.chunk_cells : N;
     const double *U = b.U + P.off;
+    const float L = P.bounded ? __uint_as_float(b.lbound[(long long)slot * b.nprob + p]) : 0.0f;
     unsigned long long best = 0ull;
     bool bad = false;
     for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      if (P.bounded) {
+        float s32, rel;
+        if (wave_sum32<2>(U, N, c, b.g1f, b.gammaf, P.inv_hf, s32, rel) &&
+            __fmul_ru(s32, __fadd_ru(1.0f, rel)) < L)
+          continue;
+      }
       const double rho = U[c];
       if (not_positive_finite(rho)) {
         bad = true;
@@ -180,7 +222,12 @@ __global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) batch_run_kernel(con
     if (b.dt_fixed <= 0.0) {
       // clear the other slot for the next step (nobody reads it during this step)
       if (blockIdx.x == 0)
-        for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) b.smax[(long long)(slot ^ 1) * b.nprob + p] = 0ull;
+        for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) {
+          b.smax[(long long)(slot ^ 1) * b.nprob + p] = 0ull;
+          b.lbound[(long long)(slot ^ 1) * b.nprob + p] = 0u;
+        }
+      dt_bound_phase(b, slot);
+      if (!grid_barrier(b.bar_count, b.bar_gen, b.flags)) return;
       dt_phase(b, slot);
       if (!grid_barrier(b.bar_count, b.bar_gen, b.flags)) return;
     }

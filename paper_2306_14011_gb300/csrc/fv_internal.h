@@ -66,6 +66,8 @@ struct BatchProblem {
   int bc[3][2];          // FV_BC_* per axis side
   double half_inv_h[3];  // 1 / (2 dx_d)
   double inv_h[2];       // 1 / dx_d
+  float inv_hf[2];       // 1 / dx_d in FP32 (time-step pre-selection)
+  int bounded;           // 1: FP32 pre-selection of the time-step reduction applies
 };
 
 struct BatchArgs {
@@ -77,10 +79,12 @@ struct BatchArgs {
   int tile[2];
   double *U, *U1, *U2;           // packed states
   unsigned long long *smax;      // [2][nprob] bits of each problem's max wave-speed sum
+  unsigned *lbound;              // [2][nprob] bits of its certified FP32 lower bound
   double *t_acc;                 // [nprob] simulated time, or null
   unsigned *flags;
   unsigned *bar_count, *bar_gen; // grid barrier words
   double g1, gamma, half_eps, efix, inv2efix, cfl, dt_fixed;
+  float g1f, gammaf;
 };
 
 // Adjoint (vector-Jacobian product) kernel: out = sum_d scale_d J_d(U)^T lam

@@ -219,6 +219,34 @@ def _config5(eps, every, steps=400, n=1024, directions=16, h=1e-6, with_magnitud
         return (grad, pairs, mags) if with_magnitudes else (grad, pairs)
 
 
+def test_step_function_composes_like_the_checkpointed_run():
+    """Five FvStepFunction steps composed by torch give the same state and the
+    same gradient, bit for bit, as FvRunFunction over the same steps (both
+    apply the same RK-step VJPs in the same order), and the gradient matches
+    the oracle's forward-mode derivative."""
+    from paper_2306_14011_gb300.autograd import FvRunFunction, FvStepFunction
+    g, U = I.isentropic_vortex(40, seed=2)
+    dt = O.time_step(g, U)
+    rng = np.random.default_rng(11)
+    w, d = rng.normal(size=U.shape), rng.normal(size=U.shape)
+    with fv.Solver(g) as s:
+        A = dev(U).requires_grad_()
+        X = A
+        for _ in range(5):
+            X = FvStepFunction.apply(X, s, dt)
+        (X * dev(w)).sum().backward()
+        B = dev(U).requires_grad_()
+        Y = FvRunFunction.apply(B, s, 5, dt, 2)
+        (Y * dev(w)).sum().backward()
+        assert torch.equal(X.detach(), Y.detach())
+        assert torch.equal(A.grad, B.grad)
+        grad = A.grad.cpu().numpy()
+    _, dUN = O.rk3_jvp(g, U, d, 5, dt)
+    assert abs(np.sum(grad * d) - np.sum(w * dUN)) <= 1e-11 * np.sum(np.abs(w * dUN))
+    with pytest.raises(ValueError):
+        FvStepFunction.apply(dev(U), None, 0.0)
+
+
 def test_config5_checkpointed_adjoint_matches_central_differences_first_order():
     """Config 5 (1024^2 vortex, 400 steps, checkpoints every 20, kinetic
     energy, h = 1e-6, 16 directions) with eps = 0 in Eq. (6): the first-order
