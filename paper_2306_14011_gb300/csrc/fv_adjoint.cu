@@ -156,14 +156,21 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
     }
     QLb[E] = bL[E];
     QRb[E] = bR[E];
-    // through the reconstruction: QL = q1 + h mm(q1-q0, q2-q1), QR = q2 - h mm(q2-q1, q3-q2)
+    // through the reconstruction: QL = q1 + h mm(q1-q0, q2-q1), QR = q2 - h mm(q2-q1, q3-q2).
+    // The picked slope's derivative is +-1 on its two cells; the selections and
+    // sign flips run on the integer pipe (isel, mul_sign), only the sums in FP64.
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double hl = h * QLb[v], hr = h * QRb[v];
-      const double c0 = pL[v] == 1 ? -hl : 0.0;
-      const double c1 = QLb[v] + (pL[v] == 1 ? hl : (pL[v] == 2 ? -hl : 0.0)) + (pR[v] == 1 ? hr : 0.0);
-      const double c2 = QRb[v] - (pR[v] == 1 ? hr : (pR[v] == 2 ? -hr : 0.0)) + (pL[v] == 2 ? hl : 0.0);
-      const double c3 = pR[v] == 2 ? -hr : 0.0;
+      const double nhl = mul_sign(hl, -1.0), nhr = mul_sign(hr, -1.0);
+      const double c0 = isel(pL[v] == 1, nhl, 0.0);
+      const double c3 = isel(pR[v] == 2, nhr, 0.0);
+      // c1 = QLb + (pL: +hl if a, -hl if b) + (pR: +hr if a)
+      // c2 = QRb + (pR: -hr if a, +hr if b) + (pL: +hl if b)
+      const double l1 = isel(pL[v] == 1, hl, isel(pL[v] == 2, nhl, 0.0));
+      const double r2 = isel(pR[v] == 1, nhr, isel(pR[v] == 2, hr, 0.0));
+      const double c1 = (QLb[v] + l1) + isel(pR[v] == 1, hr, 0.0);
+      const double c2 = (QRb[v] + r2) + isel(pL[v] == 2, hl, 0.0);
       out[(4 * v + 0) * G.fmax] = c0;
       out[(4 * v + 1) * G.fmax] = c1;
       out[(4 * v + 2) * G.fmax] = c2;
@@ -211,8 +218,11 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
   __syncthreads();
 }
 
+// Register budget: two 256-thread CTAs per SM in 2D; in 3D the 8x4x4 tile's
+// shared memory (128 KB) allows one CTA per SM anyway, so the kernel may use
+// the whole register file (the five-variable reverse pass would spill at 128).
 template <int DIM>
-__global__ void __launch_bounds__(256, 2) adjoint_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(256, DIM == 2 ? 2 : 1) adjoint_kernel(const AdjArgs a) {
   constexpr int NV = DIM + 2;
   extern __shared__ unsigned char smem_raw[];
   double *Ubox = aligned_smem(smem_raw);
