@@ -16,7 +16,7 @@ namespace fvk {
 
 // x with the sign of x flipped when s < 0 (or s is -0): x * sign(s), exact, integer pipe.
 __device__ __forceinline__ double mul_sign(double x, double s) {
-  return __longlong_as_double(dbits(x) ^ (dbits(s) & (long long)0x8000000000000000ull));
+  return __hiloint2double(__double2hiint(x) ^ (__double2hiint(s) & (int)0x80000000u), __double2loint(x));
 }
 
 template <int NT>
@@ -285,10 +285,11 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
 // Which argument the limited slope minmod(a, b) passes a derivative through:
 // 1 = a, 2 = b, 0 = none (signs differ or an argument is zero; ties -> b).
 __device__ __forceinline__ int minmod_pick(double a, double b) {
-  const long long ia = dbits(a), ib = dbits(b);
-  const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
-  if (((ia ^ ib) < 0) || ma == 0 || mb == 0) return 0;
-  return ma < mb ? 1 : 2;
+  const int ha = __double2hiint(a), hb = __double2hiint(b);
+  const unsigned la = (unsigned)__double2loint(a), lb = (unsigned)__double2loint(b);
+  const unsigned ma = (unsigned)ha & 0x7fffffffu, mb = (unsigned)hb & 0x7fffffffu;
+  if (((ha ^ hb) < 0) || (ma | la) == 0u || (mb | lb) == 0u) return 0;
+  return (ma < mb || (ma == mb && la < lb)) ? 1 : 2;
 }
 
 }  // namespace fvk

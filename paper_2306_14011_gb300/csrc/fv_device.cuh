@@ -40,14 +40,25 @@ __device__ __forceinline__ double isel(bool p, double a, double b) {
 }
 
 // minmod(a, b): 0 when the signs differ (or either is zero), else the argument
-// of smaller magnitude.  Bitwise equal to the branchy definition for finite
-// inputs (a zero argument yields a signed zero, which adds as zero).  Integer
-// compares and selects only: no FP64-pipe instruction.
+// of smaller magnitude (b on ties).  Bitwise equal to the branchy definition
+// for finite inputs (a zero argument yields a signed zero, which adds as
+// zero).  Integer compares and selects on the 32-bit halves only: written
+// with 64-bit sign masks, the compiler forms |a| and |b| as FP64 absolute
+// values, two FP64-pipe instructions per call.
 __device__ __forceinline__ double minmod(double a, double b) {
-  const long long ia = dbits(a), ib = dbits(b);
-  const long long ma = ia & 0x7fffffffffffffffll, mb = ib & 0x7fffffffffffffffll;
-  const long long m = (ma < mb) ? ia : ib;
-  return __longlong_as_double(((ia ^ ib) < 0) ? 0ll : m);
+  const int ha = __double2hiint(a), hb = __double2hiint(b);
+  const unsigned la = (unsigned)__double2loint(a), lb = (unsigned)__double2loint(b);
+  const unsigned ma = (unsigned)ha & 0x7fffffffu, mb = (unsigned)hb & 0x7fffffffu;
+  const bool a_smaller = ma < mb || (ma == mb && la < lb);
+  const bool opposite = (ha ^ hb) < 0;
+  const int h = opposite ? 0 : (a_smaller ? ha : hb);
+  const int l = opposite ? 0 : (int)(a_smaller ? la : lb);
+  return __hiloint2double(h, l);
+}
+
+// true when x is +0 or -0 (32-bit halves, integer pipe).
+__device__ __forceinline__ bool izero(double x) {
+  return (((unsigned)__double2hiint(x) & 0x7fffffffu) | (unsigned)__double2loint(x)) == 0u;
 }
 
 // x / 2 for x >= 0 on the integer pipe: decrement the biased exponent.  Exact
@@ -107,8 +118,7 @@ __device__ __forceinline__ double rcp_fp64(double x) {
 // van Leer's limited slope, 2ab / (a + b) when a and b share one strict sign,
 // else 0 (sign tests and the select on the integer pipe; 7 FP64 operations).
 __device__ __forceinline__ double vanleer(double a, double b) {
-  const long long ia = dbits(a), ib = dbits(b);
-  const bool ok = ((ia ^ ib) >= 0) && (ia & 0x7fffffffffffffffll) != 0 && (ib & 0x7fffffffffffffffll) != 0;
+  const bool ok = ((__double2hiint(a) ^ __double2hiint(b)) >= 0) && !izero(a) && !izero(b);
   const double r = (2.0 * a * b) * rcp_fp64(a + b);
   return isel(ok, r, 0.0);
 }
