@@ -75,6 +75,20 @@ __device__ __forceinline__ double half_nonneg(double x) {
   return h;
 }
 
+// x / 4 on the integer pipe: subtract 2 from the biased exponent.  Exact
+// (bitwise equal to 0.25 * x) for x = +-0 and every x of exponent field
+// 3..2046; the rest (|x| < 2^-1020, inf, NaN) take the FP64 multiply in a
+// warp-uniform branch.
+__device__ __forceinline__ double quarter(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+  const bool fast = e >= 3u && e < 0x7ffu;
+  const bool zero = izero(x);
+  double q = __hiloint2double(fast ? hi - (2 << 20) : hi, __double2loint(x));
+  if (__any_sync(__activemask(), !fast && !zero)) q = isel(!fast && !zero, 0.25 * x, q);
+  return q;
+}
+
 // true when x is not a finite positive double (x <= 0, -0, inf or NaN).
 __device__ __forceinline__ bool not_positive_finite(double x) {
   const long long ix = dbits(x);
@@ -121,6 +135,63 @@ __device__ __forceinline__ double vanleer(double a, double b) {
   const bool ok = ((__double2hiint(a) ^ __double2hiint(b)) >= 0) && !izero(a) && !izero(b);
   const double r = (2.0 * a * b) * rcp_fp64(a + b);
   return isel(ok, r, 0.0);
+}
+
+// ---- FP32 pre-selection for the time-step reduction.
+//
+// FP64 -> FP32 on the integer pipe by truncating the mantissa: relative error
+// below 2^-23 for |x| in the FP32 normal range; smaller values flush to
+// (signed) zero, larger ones and NaN become infinite.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)dbits(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned sign = hi & 0x80000000u;
+  unsigned f = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  f = e <= 0 ? sign : f;
+  f = e >= 255 ? (sign | 0x7f800000u) : f;
+  return __uint_as_float(f);
+}
+
+// The wave-speed sum s = sum_d (|u_d| + c) / dx_d of cell c (of N cells, SoA
+// state U) evaluated in FP32 (round-to-nearest operations
+// that are never contracted), and a certified relative error bound rel of it.
+// Returns false when no bound is certified.  Certification needs rho, E in
+// [2^-30, 2^30] and |m_d| <= 2^30 (no FP32 overflow or underflow on the way)
+// and a pressure p = (gamma-1)(E - k) free of strong cancellation,
+// kappa = (E + k)/(E - k) <= 1024.  A first-order bound of the FP32 error is
+// then (6 kappa + 11) 2^-24 (conversions 2^-23 each, every operation 2^-24,
+// the relative error of E - k amplified by kappa); rel = (16 kappa32 + 32)
+// 2^-24 exceeds twice that, kappa32 being kappa evaluated in FP32 (within
+// 0.1% of it when kappa <= 1024).
+template <int DIM>
+__device__ __forceinline__ bool wave_sum32(const double *U, long long N, long long c, float g1f, float gammaf,
+                                           const float *inv_hf, float &s32, float &rel) {
+  constexpr int NV = DIM + 2;
+  const float rho = f32_trunc(U[c]);
+  const float E = f32_trunc(U[(NV - 1) * N + c]);
+  bool ok = rho >= 0x1p-30f && rho <= 0x1p30f && E >= 0x1p-30f && E <= 0x1p30f;
+  const float r = __frcp_rn(rho);
+  float u[DIM];
+  float k = 0.0f;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const float m = f32_trunc(U[(1 + d) * N + c]);
+    ok = ok && fabsf(m) <= 0x1p30f;
+    u[d] = __fmul_rn(m, r);
+    k = __fadd_rn(k, __fmul_rn(m, u[d]));
+  }
+  k = 0.5f * k;
+  const float em = __fsub_rn(E, k), ep = __fadd_rn(E, k);
+  ok = ok && em > 0.0f && ep <= __fmul_rn(1024.0f, em);
+  const float c2 = __fmul_rn(__fmul_rn(gammaf, __fmul_rn(g1f, em)), r);
+  const float cs = __fsqrt_rn(c2);
+  float s = 0.0f;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) s = __fadd_rn(s, __fmul_rn(__fadd_rn(fabsf(u[d]), cs), inv_hf[d]));
+  s32 = s;
+  rel = __fmaf_ru(__fmul_ru(16.0f, __fmul_ru(ep, __frcp_ru(em))), 0x1p-24f, 32.0f * 0x1p-24f);
+  return ok;
 }
 
 // ------------------------------------------------------------ Roe flux
@@ -198,15 +269,20 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   const double a3 = (dp + rcdun) * hic2;
   const double a2 = fma(-dp, ic2, drho);
 
-  // |eigenvalues| (sign handling on the integer pipe), entropy fix
+  // |eigenvalues| (sign handling on the integer pipe), entropy fix.  Whether
+  // |lambda| < delta = efix c~ is decided in FP32 (operands truncated on the
+  // integer pipe): the fixed |lambda| equals delta at |lambda| = delta, so a
+  // decision flipped within FP32 resolution changes the flux by
+  // O(((|lambda| - delta) / delta)^2 delta), below FP64 rounding.
   double l1 = iabs(un - c);
   double l3 = iabs(un + c);
   const double l2 = iabs(un);
-  const double delta = efix * c;
-  const bool fix1 = ilt_nonneg(l1, delta), fix3 = ilt_nonneg(l3, delta);
+  const float deltaf = __fmul_rn(f32_trunc(efix), f32_trunc(c));
+  const bool fix1 = f32_trunc(l1) < deltaf, fix3 = f32_trunc(l3) < deltaf;
   // near sonic points only: a warp-uniform branch keeps the (rare) fix from
   // being computed unconditionally
   if (__any_sync(__activemask(), fix1 || fix3)) {
+    const double delta = efix * c;
     const double d2 = delta * delta, s2 = tc * inv2efix;
     l1 = isel(fix1, fma(l1, l1, d2) * s2, l1);
     l3 = isel(fix3, fma(l3, l3, d2) * s2, l3);
@@ -235,63 +311,6 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
 #pragma unroll
   for (int t = 0; t < NT; ++t) G[2 + t] = fma(QL[1], utL[t], QR[1] * utR[t]) - Dt[t];
   G[E] = fma(unL, eL, unR * eR) - DE;
-}
-
-// ---- FP32 pre-selection for the time-step reduction.
-//
-// FP64 -> FP32 on the integer pipe by truncating the mantissa: relative error
-// below 2^-23 for |x| in the FP32 normal range; smaller values flush to
-// (signed) zero, larger ones and NaN become infinite.
-__device__ __forceinline__ float f32_trunc(double x) {
-  const unsigned long long b = (unsigned long long)dbits(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
-  const unsigned sign = hi & 0x80000000u;
-  unsigned f = sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  f = e <= 0 ? sign : f;
-  f = e >= 255 ? (sign | 0x7f800000u) : f;
-  return __uint_as_float(f);
-}
-
-// The wave-speed sum s = sum_d (|u_d| + c) / dx_d of cell c (of N cells, SoA
-// state U) evaluated in FP32 (round-to-nearest operations
-// that are never contracted), and a certified relative error bound rel of it.
-// Returns false when no bound is certified.  Certification needs rho, E in
-// [2^-30, 2^30] and |m_d| <= 2^30 (no FP32 overflow or underflow on the way)
-// and a pressure p = (gamma-1)(E - k) free of strong cancellation,
-// kappa = (E + k)/(E - k) <= 1024.  A first-order bound of the FP32 error is
-// then (6 kappa + 11) 2^-24 (conversions 2^-23 each, every operation 2^-24,
-// the relative error of E - k amplified by kappa); rel = (16 kappa32 + 32)
-// 2^-24 exceeds twice that, kappa32 being kappa evaluated in FP32 (within
-// 0.1% of it when kappa <= 1024).
-template <int DIM>
-__device__ __forceinline__ bool wave_sum32(const double *U, long long N, long long c, float g1f, float gammaf,
-                                           const float *inv_hf, float &s32, float &rel) {
-  constexpr int NV = DIM + 2;
-  const float rho = f32_trunc(U[c]);
-  const float E = f32_trunc(U[(NV - 1) * N + c]);
-  bool ok = rho >= 0x1p-30f && rho <= 0x1p30f && E >= 0x1p-30f && E <= 0x1p30f;
-  const float r = __frcp_rn(rho);
-  float u[DIM];
-  float k = 0.0f;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    const float m = f32_trunc(U[(1 + d) * N + c]);
-    ok = ok && fabsf(m) <= 0x1p30f;
-    u[d] = __fmul_rn(m, r);
-    k = __fadd_rn(k, __fmul_rn(m, u[d]));
-  }
-  k = 0.5f * k;
-  const float em = __fsub_rn(E, k), ep = __fadd_rn(E, k);
-  ok = ok && em > 0.0f && ep <= __fmul_rn(1024.0f, em);
-  const float c2 = __fmul_rn(__fmul_rn(gammaf, __fmul_rn(g1f, em)), r);
-  const float cs = __fsqrt_rn(c2);
-  float s = 0.0f;
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) s = __fadd_rn(s, __fmul_rn(__fadd_rn(fabsf(u[d]), cs), inv_hf[d]));
-  s32 = s;
-  rel = __fmaf_ru(__fmul_ru(16.0f, __fmul_ru(ep, __frcp_ru(em))), 0x1p-24f, 32.0f * 0x1p-24f);
-  return ok;
 }
 
 // ------------------------------------------------------------ mbarrier / TMA (inline PTX)

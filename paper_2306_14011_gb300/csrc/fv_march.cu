@@ -285,21 +285,14 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
       const int lc = (j + 2) * G.BX + (i + 2);
 #pragma unroll
       for (int v = 0; v < NV3; ++v) {
-        double rv = cx * (Fx[v * G.nfx + fx + 1] - Fx[v * G.nfx + fx]);
+        // same accumulation as the box-tiled kernel: the stage base, then x, y, z
+        const double dFx = Fx[v * G.nfx + fx + 1] - Fx[v * G.nfx + fx];
+        double rv = (MODE == MODE_RESIDUAL) ? cx * dFx
+                                            : fma(cx, dFx, stage_base<MODE>(cur[v * G.plane + lc], a.Un + v * N + gi));
         rv = fma(cy, Fy[v * G.nfy + fy + ext0] - Fy[v * G.nfy + fy], rv);
         rv = fma(cz, Fzc[v * G.cols + c] - Fzp[v * G.cols + c], rv);
-        double outv;
-        if (MODE == MODE_RESIDUAL) {
-          outv = rv;
-          if (want_norm) nrm[v] = fma(rv, rv, nrm[v]);
-        } else if (MODE == MODE_STAGE1) {
-          outv = cur[v * G.plane + lc] + rv;
-        } else if (MODE == MODE_STAGE2) {
-          outv = fma(0.75, a.Un[v * N + gi], 0.25 * cur[v * G.plane + lc]) + rv;
-        } else {
-          outv = fma(1.0 / 3.0, a.Un[v * N + gi], (2.0 / 3.0) * cur[v * G.plane + lc]) + rv;
-        }
-        a.out[v * N + gi] = outv;
+        if (MODE == MODE_RESIDUAL && want_norm) nrm[v] = fma(rv, rv, nrm[v]);
+        a.out[v * N + gi] = rv;
       }
     }
     double *t = Fzp;  // each column's z-face buffer entries belong to one thread

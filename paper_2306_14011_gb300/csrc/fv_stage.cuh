@@ -119,10 +119,20 @@ __device__ __forceinline__ void muscl_states(double q0, double q1, double q2, do
   muscl_from_diffs<LIM>(q1, q2, q1 - q0, q2 - q1, q3 - q2, h, cL, cR, QL, QR);
 }
 
-template <int DIM, int D, int LIM>
+// The part of a stage update that does not depend on the fluxes: Us (stage
+// 1), 3/4 Un + 1/4 Us (stage 2), 1/3 Un + 2/3 Us (stage 3); 0 for the residual.
+template <int MODE>
+__device__ __forceinline__ double stage_base(double us, const double *un) {
+  if (MODE == MODE_RESIDUAL) return 0.0;
+  if (MODE == MODE_STAGE1) return us;
+  if (MODE == MODE_STAGE2) return fma(0.75, *un, quarter(us));
+  return fma(1.0 / 3.0, *un, (2.0 / 3.0) * us);
+}
+
+template <int DIM, int D, int LIM, int MODE>
 __device__ __forceinline__ void face_pass(const double *__restrict__ tile, double *__restrict__ F,
-                                          double *__restrict__ R, const StageArgs &a, const int ext[3],
-                                          const TileGeom &G, double coef) {
+                                          double *__restrict__ R, const StageArgs &a, const int o[3],
+                                          const int ext[3], const TileGeom &G, double coef) {
   constexpr int NV = DIM + 2;
   constexpr int NT = DIM - 1;
   constexpr int E = NV - 1;
@@ -208,21 +218,35 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
     }
   }
   __syncthreads();
+  // R accumulates the new value of each cell: the first axis starts from the
+  // stage base (RK modes) or from 0 (residual), so the update needs no
+  // separate addition.
   const int ncell = ext[0] * ext[1] * ((DIM == 3) ? ext[2] : 1);
   const int fstride = (D == 0) ? 1 : ((D == 1) ? fe0 : fe0 * fe1);
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const int i = c % ext[0];
     const int rr = c / ext[0];
     const int j = rr % ext[1];
     const int k = rr / ext[1];
     const int flo = (k * fe1 + j) * fe0 + i;
+    long long gi = 0;
+    int lc = 0;
+    if (D == 0 && MODE != MODE_RESIDUAL) {
+      gi = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
+      lc = (((DIM == 3) ? k + 2 : 0) * G.BY + (j + 2)) * G.BX + (i + 2);
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double dF = F[v * G.fmax + flo + fstride] - F[v * G.fmax + flo];
-      if (D == 0)
-        R[v * G.cells + c] = coef * dF;
-      else
+      if (D == 0) {
+        if (MODE == MODE_RESIDUAL)
+          R[v * G.cells + c] = coef * dF;
+        else
+          R[v * G.cells + c] = fma(coef, dF, stage_base<MODE>(tile[v * G.plane + lc], a.Un + v * N + gi));
+      } else {
         R[v * G.cells + c] = fma(coef, dF, R[v * G.cells + c]);
+      }
     }
   }
   __syncthreads();
@@ -297,9 +321,9 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
   }
   __syncthreads();
   const double dt = s_coef[0];
-  face_pass<DIM, 0, LIM>(tile, F, R, a, ext, G, s_coef[1]);
-  face_pass<DIM, 1, LIM>(tile, F, R, a, ext, G, s_coef[2]);
-  if constexpr (DIM == 3) face_pass<DIM, 2, LIM>(tile, F, R, a, ext, G, s_coef[3]);
+  face_pass<DIM, 0, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[1]);
+  face_pass<DIM, 1, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[2]);
+  if constexpr (DIM == 3) face_pass<DIM, 2, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[3]);
 
   // ---- 4. epilogue
   const int ncell = ext[0] * ext[1] * ext[2];
@@ -313,22 +337,11 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
     const int j = rr % ext[1];
     const int k = rr / ext[1];
     const long long gi = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
-    const int lc = (((DIM == 3) ? k + 2 : 0) * G.BY + (j + 2)) * G.BX + (i + 2);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double r = R[v * G.cells + c];
-      double outv;
-      if (MODE == MODE_RESIDUAL) {
-        outv = r;
-        if (want_norm) nrm[v] = fma(r, r, nrm[v]);
-      } else if (MODE == MODE_STAGE1) {
-        outv = tile[v * G.plane + lc] + r;
-      } else if (MODE == MODE_STAGE2) {
-        outv = fma(0.75, a.Un[v * N + gi], 0.25 * tile[v * G.plane + lc]) + r;
-      } else {
-        outv = fma(1.0 / 3.0, a.Un[v * N + gi], (2.0 / 3.0) * tile[v * G.plane + lc]) + r;
-      }
-      a.out[v * N + gi] = outv;
+      const double r = R[v * G.cells + c];  // the residual, or the cell's new value
+      if (MODE == MODE_RESIDUAL && want_norm) nrm[v] = fma(r, r, nrm[v]);
+      a.out[v * N + gi] = r;
     }
   }
   if (MODE == MODE_STAGE3 && a.t_acc && bx == 0 && by == 0 && bz == 0 && threadIdx.x == 0) *a.t_acc += dt;
