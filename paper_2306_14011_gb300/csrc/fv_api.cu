@@ -90,6 +90,9 @@ struct fv_ctx {
   long long norm_part_cap;
   double *X1, *X2;            // adjoint work states (lazy)
   std::vector<GraphEntry> graphs;
+  // host-pointer runs: copy-back stream and per-band events (lazy)
+  cudaStream_t copy_stream;
+  std::vector<cudaEvent_t> band_events;
   // batched contexts (ngrids > 1)
   int ngrids;
   std::vector<fv_grid> grids;
@@ -192,11 +195,14 @@ bool make_tmap(const fv_ctx *c, const double *U, const int tile[3], int march, C
 }
 
 int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, double *out,
-          const unsigned long long *smax, double dt_fixed, double *norm_part, double *t_acc, cudaStream_t st) {
+          const unsigned long long *smax, double dt_fixed, double *norm_part, double *t_acc, cudaStream_t st,
+          long long tile_begin = 0, long long tile_count = 0) {
   const fv_grid &g = c->grid;
   const fv_kernel_cfg &k = c->launch.stage[sidx];
   StageArgs a;
   memset(&a, 0, sizeof(a));
+  a.tile_begin = tile_begin;
+  a.tile_count = tile_count;
   a.Us = Us;
   a.Un = Un;
   a.out = out;
@@ -723,6 +729,56 @@ int fv_rk_step(fv_ctx *c, double *U, double dt, double *dt_used) {
   return FV_OK;
 }
 
+// The last SSP-RK3 step of a run on a host state: the dt reduction and
+// stages 1-2 as usual, then stage 3 in bands of whole tile rows (2D) or tile
+// planes (3D), each band's cells copied back to the host on a second stream
+// while the next band computes, so most of the device-to-host copy overlaps
+// the last kernel.
+int last_step_to_host(fv_ctx *c, double *Ud, double *Uh, double dt_fixed, bool cfl) {
+  const fv_grid &g = c->grid;
+  const fv_kernel_cfg &k3 = c->launch.stage[2];
+  int nt[3];
+  ntiles(g, k3.tile, nt);
+  const int slow = g.dim - 1;                     // banded axis: y in 2D, z in 3D
+  const long long per_row = (long long)nt[0] * (slow == 2 ? nt[1] : 1);  // tiles per tile row / plane
+  const int rows = nt[slow];
+  const int nb = rows < 8 ? rows : 8;
+  if (!c->copy_stream) FV_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  while ((int)c->band_events.size() < nb + 1) {
+    cudaEvent_t e;
+    FV_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->band_events.push_back(e);
+  }
+  int r;
+  const unsigned long long *sm = nullptr;
+  if (cfl) {
+    if ((r = dt_launch(c, Ud, c->stream))) return r;
+    sm = c->smax;
+  }
+  if ((r = stage(c, MODE_STAGE1, 0, Ud, Ud, c->U1, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
+  if ((r = stage(c, MODE_STAGE2, 1, c->U1, Ud, c->U2, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
+  const long long cells_per_unit = (long long)g.n[0] * (slow == 2 ? g.n[1] : 1);  // cells per grid row / plane
+  const long long N = c->ncells;
+  for (int b = 0; b < nb; ++b) {
+    const int r0 = (int)((long long)rows * b / nb), r1 = (int)((long long)rows * (b + 1) / nb);
+    if ((r = stage(c, MODE_STAGE3, 2, c->U2, Ud, Ud, sm, dt_fixed, nullptr, c->t_acc, c->stream, r0 * per_row,
+                   (long long)(r1 - r0) * per_row)))
+      return r;
+    FV_CK(cudaEventRecord(c->band_events[b], c->stream));
+    FV_CK(cudaStreamWaitEvent(c->copy_stream, c->band_events[b], 0));
+    const long long u0 = (long long)r0 * k3.tile[slow];
+    const long long u1 = std::min<long long>((long long)r1 * k3.tile[slow], g.n[slow]);
+    for (int v = 0; v < c->nv; ++v) {
+      const long long off = v * N + u0 * cells_per_unit;
+      FV_CK(cudaMemcpyAsync(Uh + off, Ud + off, sizeof(double) * (u1 - u0) * cells_per_unit, cudaMemcpyDeviceToHost,
+                            c->copy_stream));
+    }
+  }
+  FV_CK(cudaEventRecord(c->band_events[nb], c->copy_stream));
+  FV_CK(cudaStreamWaitEvent(c->stream, c->band_events[nb], 0));
+  return FV_OK;
+}
+
 int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
   if (!c || !U || nsteps < 0) return FV_EINVAL;
   int r;
@@ -777,12 +833,20 @@ int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
     remember_graph(c, GraphEntry{Ud, dbits, steps, exec});
     (pass == 0 ? gK : g1) = exec;
   }
-  for (int left = nsteps; left > 0;) {
+  // on a host state the last step runs outside the graphs, overlapping its
+  // copy back with the last stage kernel
+  for (int left = hostU ? nsteps - 1 : nsteps; left > 0;) {
     const int steps = left >= K ? K : 1;
     FV_CK(cudaGraphLaunch(steps == K ? gK : g1, c->stream));
     left -= steps;
   }
-  if (hostU) FV_CK(cudaMemcpyAsync(U, Ud, c->state_bytes, cudaMemcpyDeviceToHost, c->stream));
+  if (hostU) {
+    if (nsteps > 0) {
+      if ((r = last_step_to_host(c, Ud, U, dt_fixed, cfl))) return r;
+    } else {
+      FV_CK(cudaMemcpyAsync(U, Ud, c->state_bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
   if (t_out) {
     FV_CK(cudaMemcpyAsync(t_out, c->t_acc, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return read_flags(c);
@@ -872,6 +936,8 @@ void fv_destroy(fv_ctx *c) {
   if (c->U2) cudaFree(c->U2);
   if (c->stage_in) cudaFree(c->stage_in);
   if (c->stage_out) cudaFree(c->stage_out);
+  for (cudaEvent_t e : c->band_events) cudaEventDestroy(e);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->smax) cudaFree(c->smax);  // start of the scratch block
   if (c->norm_part) cudaFree(c->norm_part);
   if (c->X1) cudaFree(c->X1);

@@ -199,11 +199,12 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
   double *Fz1 = Fz0 + NV3 * G.cols;
   uint64_t *mbar = reinterpret_cast<uint64_t *>(Fz1 + NV3 * G.cols);
 
-  int b = blockIdx.x;
-  const int bx = b % a.ntile[0];
+  const long long tix = a.tile_begin + blockIdx.x;  // linear tile index
+  long long b = tix;
+  const int bx = (int)(b % a.ntile[0]);
   b /= a.ntile[0];
-  const int by = b % a.ntile[1];
-  const int bz = b / a.ntile[1];
+  const int by = (int)(b % a.ntile[1]);
+  const int bz = (int)(b / a.ntile[1]);
   const int o[2] = {bx * a.tile[0], by * a.tile[1]};
   const int ext0 = min(a.tile[0], a.n[0] - o[0]), ext1 = min(a.tile[1], a.n[1] - o[1]);
   const int z0 = bz * a.tile[2];
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
     Fzp = Fzc;
     Fzc = t;
   }
-  if (MODE == MODE_STAGE3 && a.t_acc && blockIdx.x == 0 && threadIdx.x == 0) *a.t_acc += dt;
+  if (MODE == MODE_STAGE3 && a.t_acc && tix == 0 && threadIdx.x == 0) *a.t_acc += dt;
 
   if (want_norm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
       double sum = 0.0;
       const int nw = (blockDim.x + 31) >> 5;
       for (int q = 0; q < nw; ++q) sum += red[threadIdx.x][q];
-      a.norm_part[(long long)blockIdx.x * NV3 + threadIdx.x] = sum;
+      a.norm_part[tix * NV3 + threadIdx.x] = sum;
     }
   }
 }
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
 template <int LIM>
 cudaError_t launch_march_lim(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st) {
   const size_t smem = march_smem_bytes(a.tile);
-  const long long nblk = (long long)a.ntile[0] * a.ntile[1] * a.ntile[2];
+  const long long nblk = a.tile_count > 0 ? a.tile_count : (long long)a.ntile[0] * a.ntile[1] * a.ntile[2] - a.tile_begin;
   const dim3 grid((unsigned)nblk), block(threads);
   switch (mode) {
     case MODE_RESIDUAL: march_kernel<MODE_RESIDUAL, LIM><<<grid, block, smem, st>>>(*tmap, a); break;

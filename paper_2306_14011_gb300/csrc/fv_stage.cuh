@@ -405,18 +405,18 @@ __global__ void __launch_bounds__(DIM == 2 ? 256 : kStage3dMaxThreads, FV_STAGE_
     }
     __syncthreads();
   }
-  int b = blockIdx.x;
-  const int bx = b % a.ntile[0];
+  long long b = a.tile_begin + blockIdx.x;
+  const int bx = (int)(b % a.ntile[0]);
   b /= a.ntile[0];
-  const int by = b % a.ntile[1];
-  const int bz = b / a.ntile[1];
+  const int by = (int)(b % a.ntile[1]);
+  const int bz = (int)(b / a.ntile[1]);
   tile_work<DIM, MODE, LIM>(&tmap, a, bx, by, bz, tile, mbar, 0u, s_coef, red);
 }
 
 template <int DIM, int LIM>
 cudaError_t launch_stage_lim(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st) {
   const size_t smem = stage_smem_bytes(DIM, a.tile);
-  const long long nblk = (long long)a.ntile[0] * a.ntile[1] * a.ntile[2];
+  const long long nblk = a.tile_count > 0 ? a.tile_count : (long long)a.ntile[0] * a.ntile[1] * a.ntile[2] - a.tile_begin;
   const dim3 grid((unsigned)nblk), block(threads);
   switch (mode) {
     case MODE_RESIDUAL: stage_kernel<DIM, MODE_RESIDUAL, LIM><<<grid, block, smem, st>>>(*tmap, a); break;

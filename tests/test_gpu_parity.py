@@ -203,6 +203,31 @@ def test_host_pointer_path_equals_device_path():
         assert np.array_equal(Ud.cpu().numpy(), Uh)
 
 
+@pytest.mark.parametrize("case,launch", [
+    ("ragged70x45_mixed_bc", None), ("kh256", None), ("tiny4x4", None),
+    ("box3d_36x20x14_mixed", None), ("tgv24", dict(tile=(16, 8, 5), threads=256, march=1)),
+    ("tgv24", dict(tile=(8, 8, 2), threads=128, march=0))])
+@pytest.mark.parametrize("nsteps", [1, 2, 17])
+def test_host_state_runs_equal_device_runs(case, launch, nsteps):
+    """On a host state the last step's stage 3 runs in bands of tile rows
+    (planes) whose cells are copied back while the next band computes; the
+    result, and the simulated time, equal the device run bit for bit."""
+    g, U = CASES[case]()
+    d = fv.launch_to_dict(fv.fv_default_launch(g))
+    if launch:
+        for s_ in range(3):
+            d["stage"][s_].update(launch)
+    with fv.Solver(g, launch=d) as s:
+        Ud = dev(U)
+        td = s.run(Ud, nsteps, return_time=True)
+        Uh = torch.from_numpy(U.copy()).pin_memory().numpy()
+        th = s.run(Uh, nsteps, return_time=True)
+        Up = U.copy()  # pageable host memory
+        tp = s.run(Up, nsteps, return_time=True)
+    assert np.array_equal(Ud.cpu().numpy(), Uh) and np.array_equal(Uh, Up)
+    assert td == th == tp
+
+
 def test_graph_replay_equals_single_steps():
     g, U = I.kelvin_helmholtz(128, seed=1)
     with fv.Solver(g) as s:
