@@ -320,6 +320,18 @@ int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const double *U, d
  * precision).  Stream-ordered on `stream`. */
 int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, void *stream);
 
+/* Failure-path check of the library's bounded device waits (not in the
+ * paper; for tests): one CTA waits on something that never completes --
+ * kind 0: an mbarrier no copy arrives on (the wait of every TMA tile load),
+ * kind 1: a word nothing changes (the wait of the batched kernel's grid
+ * barrier) -- gives up after limit_seconds (0 < limit <= 10), raises its
+ * timeout flag and returns.  Synchronises `stream` and returns FV_ETIMEOUT
+ * when the wait ran out as designed (the device stays usable), FV_OK if it
+ * unexpectedly completed, FV_EINVAL for a bad kind or limit, FV_ECUDA or
+ * FV_ENOMEM on a CUDA failure.  Allocates and frees 8 bytes of device
+ * memory. */
+int fv_debug_wait(int kind, double limit_seconds, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -952,6 +952,26 @@ void fv_destroy(fv_ctx *c) {
   delete c;
 }
 
+int fv_debug_wait(int kind, double limit_seconds, void *stream) {
+  if ((kind != 0 && kind != 1) || !(limit_seconds > 0.0) || !(limit_seconds <= 10.0)) return FV_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned *buf = nullptr;  // [0] the word nobody changes, [1] flags
+  if (cudaMalloc(&buf, 2 * sizeof(unsigned)) != cudaSuccess) return cuda_fail(cudaErrorMemoryAllocation);
+  int r = FV_OK;
+  unsigned flags = 0;
+  if (cudaMemsetAsync(buf, 0, 2 * sizeof(unsigned), st) != cudaSuccess ||
+      launch_debug_wait(kind, (unsigned long long)(limit_seconds * 1e9), buf, buf + 1, st) != cudaSuccess ||
+      cudaMemcpyAsync(&flags, buf + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    r = FV_ECUDA;
+  } else if (flags & FLAG_TIMEOUT) {
+    r = FV_ETIMEOUT;
+  }
+  cudaFree(buf);
+  return r;
+}
+
 int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, void *stream) {
   if (!x || !out_rsqrt || !out_rcp || n < 0) return FV_EINVAL;
   FV_CK(launch_debug_math(x, out_rsqrt, out_rcp, n, static_cast<cudaStream_t>(stream)));

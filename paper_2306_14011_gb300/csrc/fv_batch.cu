@@ -33,16 +33,9 @@ __device__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned *flags) {
       atomicExch(count, 0u);
       __threadfence();
       atomicAdd(gen, 1u);
-    } else {
-      const uint64_t t0 = globaltimer_ns();
-      while (*vgen == g) {
-        if (globaltimer_ns() - t0 > kBarrierWaitNs) {
-          atomicOr(flags, FLAG_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
+    } else if (!spin_while_equal(vgen, g, kBarrierWaitNs)) {
+      atomicOr(flags, FLAG_TIMEOUT);
+      ok = 0;
     }
     __threadfence();
   }

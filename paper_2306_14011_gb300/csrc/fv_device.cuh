@@ -350,6 +350,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   }
 }
 
+// Spin while *word == value, giving up after limit_ns of wall time (checked
+// every poll, with a short sleep between polls).  Returns false on timeout.
+__device__ __forceinline__ bool spin_while_equal(const volatile unsigned *word, unsigned value, uint64_t limit_ns) {
+  const uint64_t t0 = globaltimer_ns();
+  while (*word == value) {
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
 // TMA tiled loads into shared memory, completing on an mbarrier.
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint32_t bar) {

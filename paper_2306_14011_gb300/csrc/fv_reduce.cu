@@ -132,6 +132,32 @@ __global__ void __launch_bounds__(1024) dt_kernel(const DtArgs a) {
   }
 }
 
+// Failure-path check of the bounded waits: kind 0 waits on an mbarrier that
+// no copy completes (the tile-load wait), kind 1 on a word that nothing
+// changes (the grid-barrier wait); both give up after limit_ns, raise
+// FLAG_TIMEOUT in *flags and return.
+__global__ void debug_wait_kernel(int kind, unsigned long long limit_ns, unsigned *word, unsigned *flags) {
+  __shared__ __align__(8) uint64_t bar;
+  bool ok;
+  if (kind == 0) {
+    if (threadIdx.x == 0) {
+      mbar_init(smem_u32(&bar), 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    ok = mbar_wait_bounded(smem_u32(&bar), 0u, limit_ns);
+  } else {
+    ok = spin_while_equal(word, 0u, limit_ns);
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(flags, FLAG_TIMEOUT);
+}
+
+cudaError_t launch_debug_wait(int kind, unsigned long long limit_ns, unsigned *word, unsigned *flags,
+                              cudaStream_t st) {
+  debug_wait_kernel<<<1, 32, 0, st>>>(kind, limit_ns, word, flags);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dt(const DtArgs &a, int blocks, int threads, cudaStream_t st) {
   if (a.dim == 2) {
     if (a.bounded) dt_bound_kernel<2><<<blocks, threads, 0, st>>>(a);

@@ -110,6 +110,8 @@ def load() -> C.CDLL:
         L.fv_tune.restype = C.c_int
         L.fv_tune_space.argtypes = [C.c_int, P(C.c_int), P(C.c_double)]
         L.fv_tune_space.restype = C.c_int
+        L.fv_debug_wait.argtypes = [C.c_int, C.c_double, _VP]
+        L.fv_debug_wait.restype = C.c_int
         L.fv_layout.argtypes = [_VP, P(C.c_longlong), C.c_int]
         L.fv_layout.restype = C.c_int
         L.fv_adjoint_vjp.argtypes = [_VP, C.c_int, _VP, _VP, C.c_double, _VP]
@@ -336,6 +338,13 @@ def fv_tune_space(dim: int):
     size = C.c_double(0.0)
     _check(load().fv_tune_space(dim, C.byref(n), C.byref(size)), "fv_tune_space")
     return n.value, size.value
+
+
+def fv_debug_wait(kind: int, limit_seconds: float, stream=None):
+    """Run one of the library's bounded device waits on something that never
+    completes (kind 0: the tile-load mbarrier wait, 1: the grid-barrier spin);
+    raises FvError(FV_ETIMEOUT) when it gives up as designed."""
+    _check(load().fv_debug_wait(int(kind), float(limit_seconds), _stream_handle(stream)), "fv_debug_wait")
 
 
 FV_VJP_RESIDUAL, FV_VJP_RKSTEP = 0, 1

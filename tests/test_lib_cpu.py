@@ -96,3 +96,10 @@ def test_tuning_space_sizes():
     assert paper_points == 10 ** 7 * 12 ** 7 and f"{paper_points:.2e}" == "3.58e+14"
     with pytest.raises(fv.FvError):
         fv.fv_tune_space(4)
+
+
+def test_debug_wait_rejects_bad_arguments_on_the_host():
+    for kind, limit in [(2, 0.1), (-1, 0.1), (0, 0.0), (1, -1.0), (0, 11.0), (1, float("nan"))]:
+        with pytest.raises(fv.FvError) as e:
+            fv.fv_debug_wait(kind, limit, stream=0)
+        assert e.value.status == fv.FV_EINVAL
