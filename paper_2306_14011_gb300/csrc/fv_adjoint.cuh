@@ -67,7 +67,7 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   }
   const double H = fma(wL, HL, wR * HR);
   const double rho = sL * sR;
-  const double hq = 0.5 * q2;
+  const double hq = half_nonneg(q2);
   const double c2 = g1 * (H - hq);
   const double tc = rsqrt_fp64(c2);
   const double c = c2 * tc;
@@ -76,18 +76,20 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   const double dun = unR - unL;
   const double rc = rho * c;
   const double rcdun = rc * dun;
-  const double hic2 = 0.5 * ic2;
+  const double hic2 = half_nonneg(ic2);
   const double a1 = (dp - rcdun) * hic2;
   const double a3 = (dp + rcdun) * hic2;
   const double a2 = fma(-dp, ic2, QR[0] - QL[0]);
   const double x1 = un - c, x3 = un + c;
   const double m1 = iabs(x1), m3 = iabs(x3), l2 = iabs(un);
-  const double delta = efix * c;
-  const bool fix1 = ilt_nonneg(m1, delta), fix3 = ilt_nonneg(m3, delta);
-  const double s2 = tc * inv2efix;
-  double l1 = m1, l3 = m3;
+  // the fix decision of roe_2F (FP32 copies), so both differentiate one function
+  const float deltaf = __fmul_rn(f32_trunc(efix), f32_trunc(c));
+  const bool fix1 = f32_trunc(m1) < deltaf, fix3 = f32_trunc(m3) < deltaf;
+  double l1 = m1, l3 = m3, delta = 0.0, s2 = 0.0;
   const bool anyfix = __any_sync(__activemask(), fix1 || fix3);
   if (anyfix) {
+    delta = efix * c;
+    s2 = tc * inv2efix;
     const double d2 = delta * delta;
     l1 = isel(fix1, fma(m1, m1, d2) * s2, m1);
     l3 = isel(fix3, fma(m3, m3, d2) * s2, m3);
@@ -188,24 +190,24 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   pRb += dpb;
   pLb -= dpb;
   // ic2 = tc^2 ; c = c2 tc ; tc = c2^(-1/2)
-  tcb = fma(ic2b, 2.0 * tc, tcb);
+  tcb = fma(ic2b, scale_pow2<1>(tc), tcb);
   tcb = fma(cb, c2, tcb);
   double c2b = cb * tc;
-  c2b = fma(tcb, -0.5 * tc * ic2, c2b);
+  c2b = fma(tcb, -(scale_pow2<-1>(tc) * ic2), c2b);
   // c2 = g1 (H - hq)
   Hb = fma(c2b, g1, Hb);
   hqb = fma(-c2b, g1, hqb);
-  const double q2b = 0.5 * hqb;
+  // q2b = hqb / 2 enters as 2 q2b un = hqb un and 2 q2b ut = hqb ut
   // rho = sL sR
   double sLb = rhob * sR, sRb = rhob * sL;
   // H = wL HL + wR HR
   double wLb = Hb * HL, wRb = Hb * HR;
   const double HLb = Hb * wL, HRb = Hb * wR;
   // q2 = un^2 + sum ut^2
-  unb = fma(q2b, 2.0 * un, unb);
+  unb = fma(hqb, un, unb);
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    utb[t] = fma(q2b, 2.0 * ut[t], utb[t]);
+    utb[t] = fma(hqb, ut[t], utb[t]);
     // ut = wL utL + wR utR
     wLb = fma(utb[t], utL[t], wLb);
     wRb = fma(utb[t], utR[t], wRb);
@@ -248,8 +250,8 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   rLb = fma(unLb, QL[1], rLb);
   double tLb = sLb * QL[0];
   double rhoLb = sLb * tL;
-  tLb = fma(rLb, 2.0 * tL, tLb);
-  rhoLb = fma(tLb, -0.5 * tL * rL, rhoLb);
+  tLb = fma(rLb, scale_pow2<1>(tL), tLb);
+  rhoLb = fma(tLb, -(scale_pow2<-1>(tL) * rL), rhoLb);
   QLb[0] = rhoLb - drhob;
   QLb[1] = mnLb;
   QLb[E] = ELb;
@@ -275,8 +277,8 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   rRb = fma(unRb, QR[1], rRb);
   double tRb = sRb * QR[0];
   double rhoRb = sRb * tR;
-  tRb = fma(rRb, 2.0 * tR, tRb);
-  rhoRb = fma(tRb, -0.5 * tR * rR, rhoRb);
+  tRb = fma(rRb, scale_pow2<1>(tR), tRb);
+  rhoRb = fma(tRb, -(scale_pow2<-1>(tR) * rR), rhoRb);
   QRb[0] = rhoRb + drhob;
   QRb[1] = mnRb;
   QRb[E] = ERb;

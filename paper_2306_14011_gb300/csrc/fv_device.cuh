@@ -75,19 +75,25 @@ __device__ __forceinline__ double half_nonneg(double x) {
   return h;
 }
 
-// x / 4 on the integer pipe: subtract 2 from the biased exponent.  Exact
-// (bitwise equal to 0.25 * x) for x = +-0 and every x of exponent field
-// 3..2046; the rest (|x| < 2^-1020, inf, NaN) take the FP64 multiply in a
+// x * 2^K (K = -2, -1 or 1) on the integer pipe: add K to the biased
+// exponent.  Exact (bitwise equal to the FP64 product) for x = +-0 and every
+// x whose exponent field stays within 1..2046; the rest (results near the
+// subnormal range or overflowing, inf, NaN) take the FP64 multiply in a
 // warp-uniform branch.
-__device__ __forceinline__ double quarter(double x) {
+template <int K>
+__device__ __forceinline__ double scale_pow2(double x) {
   const int hi = __double2hiint(x);
-  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
-  const bool fast = e >= 3u && e < 0x7ffu;
+  const int e = (int)(((unsigned)hi >> 20) & 0x7ffu);
+  const bool fast = e >= 1 && e <= 2046 && e + K >= 1 && e + K <= 2046;
   const bool zero = izero(x);
-  double q = __hiloint2double(fast ? hi - (2 << 20) : hi, __double2loint(x));
-  if (__any_sync(__activemask(), !fast && !zero)) q = isel(!fast && !zero, 0.25 * x, q);
+  double q = __hiloint2double(fast ? hi + K * (1 << 20) : hi, __double2loint(x));
+  if (__any_sync(__activemask(), !fast && !zero)) {
+    const double f = K == -2 ? 0.25 : (K == -1 ? 0.5 : 2.0);
+    q = isel(!fast && !zero, f * x, q);
+  }
   return q;
 }
+__device__ __forceinline__ double quarter(double x) { return scale_pow2<-2>(x); }
 
 // true when x is not a finite positive double (x <= 0, -0, inf or NaN).
 __device__ __forceinline__ bool not_positive_finite(double x) {
