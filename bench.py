@@ -549,7 +549,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune", action="store_true", help="also run the autotuner and time its launch")
-    ap.add_argument("--tune-samples", type=int, default=300)
+    ap.add_argument("--tune-samples", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

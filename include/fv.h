@@ -230,7 +230,7 @@ int fv_mlp_predict(int nl, const int *sizes, const double *params, const double 
 
 /* Tuning options; zero fields take the defaults in brackets. */
 typedef struct fv_tune_opts {
-  int samples;     /* random configurations timed, split 75% train / 25% test [400] */
+  int samples;     /* random configurations timed, split 75% train / 25% test [1000] */
   int steps;       /* SSP-RK3 steps timed per measurement, after one warm-up step [2] */
   int repeats;     /* measurements per configuration, median taken [1] */
   int candidates;  /* random configurations scored by the network [200000] */

@@ -183,7 +183,7 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
   fv_tune_opts o;
   memset(&o, 0, sizeof(o));
   if (opts_in) o = *opts_in;
-  if (o.samples <= 0) o.samples = 400;
+  if (o.samples <= 0) o.samples = 1000;
   if (o.steps <= 0) o.steps = 2;
   if (o.repeats <= 0) o.repeats = 1;
   if (o.candidates <= 0) o.candidates = 200000;
