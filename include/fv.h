@@ -110,7 +110,8 @@ typedef struct fv_launch {
 typedef struct fv_ctx fv_ctx;
 
 /* Fill *l with the default launch configuration for grid g (one tile shape
- * and thread count for all stages): 2D 32x32 box tiles with 256 threads; 3D
+ * and thread count for all stages): 2D 32x32 box tiles with 160 threads (256
+ * in a batched context created without a launch); 3D
  * 8x8x8 box tiles with 192 threads; time-step reduction 512 threads, two
  * CTAs per SM.  Returns FV_EINVAL for a bad grid. */
 int fv_default_launch(const fv_grid *g, fv_launch *l);
