@@ -321,6 +321,14 @@ int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const double *U, d
  * precision).  Stream-ordered on `stream`. */
 int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, void *stream);
 
+/* The kernels' integer-pipe replacements of FP64 operations, applied to n
+ * device doubles (for tests): out[i] = op(x[i], y[i]) with op 0: x/2 for
+ * x >= 0 (half_nonneg), 1: x/4, 2: x/2, 3: 2x (exponent shifts), 4:
+ * minmod(x, y), 5: |x|.  Each must equal its FP64 definition bit for bit.
+ * y is read only by op 4.  Stream-ordered, no synchronisation.  FV_EINVAL
+ * for a bad op or pointer. */
+int fv_debug_bits(int op, const double *x, const double *y, double *out, long n, void *stream);
+
 /* Failure-path check of the library's bounded device waits (not in the
  * paper; for tests): one CTA waits on something that never completes --
  * kind 0: an mbarrier no copy arrives on (the wait of every TMA tile load),

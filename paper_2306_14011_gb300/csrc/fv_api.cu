@@ -980,6 +980,12 @@ int fv_debug_wait(int kind, double limit_seconds, void *stream) {
   return r;
 }
 
+int fv_debug_bits(int op, const double *x, const double *y, double *out, long n, void *stream) {
+  if (op < 0 || op > 5 || !x || !out || n < 0 || (op == 4 && !y)) return FV_EINVAL;
+  FV_CK(launch_debug_bits(op, x, y, out, n, static_cast<cudaStream_t>(stream)));
+  return FV_OK;
+}
+
 int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, void *stream) {
   if (!x || !out_rsqrt || !out_rcp || n < 0) return FV_EINVAL;
   FV_CK(launch_debug_math(x, out_rsqrt, out_rcp, n, static_cast<cudaStream_t>(stream)));

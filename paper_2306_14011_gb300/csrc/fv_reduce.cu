@@ -203,6 +203,33 @@ __global__ void debug_math_kernel(const double *x, double *o1, double *o2, long 
   }
 }
 
+// The integer-pipe helpers on arbitrary inputs: out[i] = op(x[i], y[i]) with
+// op 0: half_nonneg(x), 1: scale_pow2<-2>(x), 2: scale_pow2<-1>(x),
+// 3: scale_pow2<1>(x), 4: minmod(x, y), 5: iabs(x).
+__global__ void debug_bits_kernel(int op, const double *x, const double *y, double *out, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    double r;
+    switch (op) {
+      case 0: r = half_nonneg(v); break;
+      case 1: r = scale_pow2<-2>(v); break;
+      case 2: r = scale_pow2<-1>(v); break;
+      case 3: r = scale_pow2<1>(v); break;
+      case 4: r = minmod(v, y[i]); break;
+      default: r = iabs(v); break;
+    }
+    out[i] = r;
+  }
+}
+
+cudaError_t launch_debug_bits(int op, const double *x, const double *y, double *out, long n, cudaStream_t st) {
+  long blocks = (n + 255) / 256;
+  if (blocks > 1216) blocks = 1216;
+  if (blocks < 1) blocks = 1;
+  debug_bits_kernel<<<(unsigned)blocks, 256, 0, st>>>(op, x, y, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_debug_math(const double *x, double *o1, double *o2, long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   long blocks = (n + 255) / 256;

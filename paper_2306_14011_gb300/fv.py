@@ -112,6 +112,8 @@ def load() -> C.CDLL:
         L.fv_tune_space.restype = C.c_int
         L.fv_debug_wait.argtypes = [C.c_int, C.c_double, _VP]
         L.fv_debug_wait.restype = C.c_int
+        L.fv_debug_bits.argtypes = [C.c_int, _VP, _VP, _VP, C.c_long, _VP]
+        L.fv_debug_bits.restype = C.c_int
         L.fv_layout.argtypes = [_VP, P(C.c_longlong), C.c_int]
         L.fv_layout.restype = C.c_int
         L.fv_adjoint_vjp.argtypes = [_VP, C.c_int, _VP, _VP, C.c_double, _VP]
@@ -354,6 +356,12 @@ def fv_adjoint_vjp(ctx: int, what: int, U, lam, dt: float, out):
     """out = (dR/dU)^T lam (what = FV_VJP_RESIDUAL) or (dU_{n+1}/dU_n)^T lam for
     one SSP-RK3 step with fixed dt (FV_VJP_RKSTEP).  Device tensors."""
     _check(load().fv_adjoint_vjp(ctx, what, _ptr(U), _ptr(lam), float(dt), _ptr(out)), "fv_adjoint_vjp")
+
+
+def fv_debug_bits(op: int, x, out, y=None, stream=None):
+    """out = op(x[, y]) with the kernels' integer-pipe helpers (see fv.h)."""
+    _check(load().fv_debug_bits(int(op), _ptr(x), None if y is None else _ptr(y), _ptr(out), x.numel(),
+                                _stream_handle(stream)), "fv_debug_bits")
 
 
 def fv_debug_math(x, out_rsqrt, out_rcp, stream=None):
