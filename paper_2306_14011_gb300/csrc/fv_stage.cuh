@@ -8,12 +8,15 @@
 //      without a tensor map (odd nx, tiny grids) every cell is a plain load;
 //   2. per axis d, computes every face flux of the tile exactly once: MUSCL
 //      face states of Eq. (6) (eps/2 * minmod slope) and the Roe flux, into a
-//      shared-memory face buffer; faces are spread over all threads so warps
-//      stay full;
-//   3. accumulates R_v = sum_d coef_d (F_{k+1/2} - F_{k-1/2}) per cell in
-//      shared memory, the flux-difference form of Eq. (5);
-//   4. writes the residual, or the SSP-RK3 stage combination of Eq. (4)
-//      discretised in time, for its cells (coalesced along x).
+//      shared-memory face buffer; each thread takes a run of consecutive faces
+//      along the normal, carrying the stencil differences from face to face;
+//   3. accumulates per cell, in shared memory, sum_d coef_d (F_{k+1/2} -
+//      F_{k-1/2}) -- the flux-difference form of Eq. (5) -- starting, in the
+//      RK modes, from the stage's base value (U^s, 3/4 U^n + 1/4 U^s or
+//      1/3 U^n + 2/3 U^s), so the accumulator ends as the SSP-RK3 stage of
+//      Eq. (4) discretised in time;
+//   4. writes the residual or the new stage state for its cells (coalesced
+//      along x).
 // Faces on a tile boundary are computed by both neighbouring CTAs (a
 // 1/tile_x + 1/tile_y [+ 1/tile_z] overhead); inside a tile each face is
 // evaluated once.
@@ -254,7 +257,7 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
 
 // All the work of one tile: stage the tile (TMA with mbarrier `bar` at parity
 // `phase`, or plain loads), compute the face fluxes axis by axis, accumulate
-// the residual and write the epilogue.  `tile` is the CTA's dynamic shared
+// the residual (or the new stage state) and write it.  `tile` is the CTA's dynamic shared
 // memory (128-byte aligned); s_coef and red are static shared scratch.
 // Returns false (uniformly across the CTA) if the tile load timed out.
 template <int DIM, int MODE, int LIM = FV_LIM_MINMOD>
