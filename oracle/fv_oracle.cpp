@@ -62,22 +62,23 @@ using namespace orc;
 
 extern "C" {
 
-// Spatial residual R_h of Eq. (5) (face areas included, S = 0).
+// Spatial residual R_h of Eq. (5) (face areas included; S: the cell-averaged
+// source, same layout as U, or NULL for S = 0).
 // U, R: [nv][nz][ny][nx] float64.  Returns 0.
-int orc_residual(const Grid *g, const Scheme *s, const double *U, double *R) {
-  residual(*g, *s, U, R);
+int orc_residual(const Grid *g, const Scheme *s, const double *U, double *R, const double *S) {
+  residual(*g, *s, U, R, S);
   return 0;
 }
 
 // The residual evaluated in extended precision (long double: 64-bit or
 // 113-bit significand depending on the host) from the same double inputs,
 // for measuring the rounding error of FP64 evaluations.
-int orc_residual_ext(const Grid *g, const Scheme *s, const double *U, double *R) {
+int orc_residual_ext(const Grid *g, const Scheme *s, const double *U, double *R, const double *S) {
   Layout L(*g);
   size_t N = L.cells() * L.nv;
   std::vector<long double> X(N), Y(N);
   for (size_t c = 0; c < N; ++c) X[c] = U[c];
-  residual(*g, *s, X.data(), Y.data());
+  residual(*g, *s, X.data(), Y.data(), S);
   for (size_t c = 0; c < N; ++c) R[c] = (double)Y[c];
   return 0;
 }
@@ -87,10 +88,10 @@ double orc_time_step(const Grid *g, const Scheme *s, const double *U) { return t
 
 // One SSP-RK3 step in place.  dt <= 0: use the CFL step of U.
 // Returns the dt used, or -1 when the state is non-physical.
-double orc_rk3_step(const Grid *g, const Scheme *s, double *U, double dt) {
+double orc_rk3_step(const Grid *g, const Scheme *s, double *U, double dt, const double *S) {
   if (dt <= 0.0) dt = time_step(*g, *s, U);
   if (dt <= 0.0) return -1.0;
-  rk3_step(*g, *s, U, dt);
+  rk3_step(*g, *s, U, dt, S);
   return dt;
 }
 
@@ -98,14 +99,14 @@ double orc_rk3_step(const Grid *g, const Scheme *s, double *U, double dt) {
 // takes the CFL step of its starting state, and with t_end > 0 the last step
 // is shortened to land on t_end (steps stop there).  Returns the time reached,
 // or -1 when the state became non-physical.
-double orc_run(const Grid *g, const Scheme *s, double *U, int nsteps, double dt_fixed, double t_end) {
+double orc_run(const Grid *g, const Scheme *s, double *U, int nsteps, double dt_fixed, double t_end, const double *S) {
   double t = 0.0;
   for (int n = 0; n < nsteps; ++n) {
     if (t_end > 0.0 && t >= t_end) break;
     double dt = dt_fixed > 0.0 ? dt_fixed : time_step(*g, *s, U);
     if (dt <= 0.0) return -1.0;
     if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
-    rk3_step(*g, *s, U, dt);
+    rk3_step(*g, *s, U, dt, S);
     t += dt;
   }
   return t;

@@ -11,7 +11,7 @@
 //     limiter Psi = minmod, eps and kappa as parameters              [Eq. (6)]
 //   * Roe approximate Riemann flux with Harten's entropy fix on the
 //     acoustic waves (the paper leaves the flux function unnamed)
-//   * spatial residual R_h = sum over faces of F*ds (source S = 0)  [Eq. (5)]
+//   * spatial residual R_h = sum over faces of F*ds - |Omega| S     [Eq. (5)]
 //   * semi-discrete form |Omega| dU/dt + R_h = 0                    [Eq. (4)]
 //     advanced with the three-stage SSP Runge-Kutta scheme of Shu-Osher
 //     (the paper says "explicit Runge-Kutta", Sec. 3.2)
@@ -269,13 +269,15 @@ void pad(const Grid &g, const Layout &L, const T *U, std::vector<T> &P) {
         }
 }
 
-// Spatial residual of Eq. (5) with S = 0: for every cell,
-//   R_k = sum over its faces of F.n ds = sum_d ds_d (F_{k+1/2,d} - F_{k-1/2,d}),
+// Spatial residual of Eq. (5): for every cell,
+//   R_k = sum over its faces of F.n ds - |Omega| S_k
+//       = sum_d ds_d (F_{k+1/2,d} - F_{k-1/2,d}) - |Omega| S_k,
 // where ds_d is the area of a face normal to axis d (dy in 2D for x-faces,
-// dy*dz in 3D) and F_{k+1/2,d} the Roe flux between the MUSCL states of Eq. (6).
+// dy*dz in 3D), F_{k+1/2,d} the Roe flux between the MUSCL states of Eq. (6)
+// (inviscid: no viscous flux) and S the cell-averaged source (S = NULL: 0).
 // Each face flux is evaluated once, stored, and read by both cells that share it.
 template <class T>
-void residual(const Grid &g, const Scheme &s, const T *U, T *R) {
+void residual(const Grid &g, const Scheme &s, const T *U, T *R, const double *S = nullptr) {
   Layout L(g);
   std::vector<T> P;
   pad(g, L, U, P);
@@ -318,6 +320,11 @@ void residual(const Grid &g, const Scheme &s, const T *U, T *R) {
         R[(size_t)v * ncell + cidx] += (F[(size_t)v * nface + hi] - F[(size_t)v * nface + lo]) * ds;
     }
   }
+  if (S) {
+    double vol = 1.0;
+    for (int a = 0; a < L.dim; ++a) vol *= L.h[a];
+    for (long c = 0; c < ncell * nv; ++c) R[c] = R[c] - vol * T(S[c]);
+  }
 }
 
 // Largest stable time step of the explicit scheme,
@@ -354,17 +361,17 @@ double time_step(const Grid &g, const Scheme &s, const T *U) {
 //   U2 = 3/4 U + 1/4 (U1 + dt L(U1))
 //   U  = 1/3 U + 2/3 (U2 + dt L(U2))
 template <class T>
-void rk3_step(const Grid &g, const Scheme &s, T *U, double dt) {
+void rk3_step(const Grid &g, const Scheme &s, T *U, double dt, const double *S = nullptr) {
   Layout L(g);
   const size_t N = L.cells() * L.nv;
   double vol = 1.0;
   for (int a = 0; a < L.dim; ++a) vol *= L.h[a];
   std::vector<T> R(N), U1(N), U2(N);
-  residual(g, s, U, R.data());
+  residual(g, s, U, R.data(), S);
   for (size_t c = 0; c < N; ++c) U1[c] = U[c] + dt * (-R[c] / vol);
-  residual(g, s, U1.data(), R.data());
+  residual(g, s, U1.data(), R.data(), S);
   for (size_t c = 0; c < N; ++c) U2[c] = 0.75 * U[c] + 0.25 * (U1[c] + dt * (-R[c] / vol));
-  residual(g, s, U2.data(), R.data());
+  residual(g, s, U2.data(), R.data(), S);
   for (size_t c = 0; c < N; ++c) U[c] = (1.0 / 3.0) * U[c] + (2.0 / 3.0) * (U2[c] + dt * (-R[c] / vol));
 }
 

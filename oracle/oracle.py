@@ -49,14 +49,14 @@ def load_library(path: str):
     L = C.CDLL(path)
     if True:
         GP, SP = C.POINTER(Grid), C.POINTER(Scheme)
-        L.orc_residual.argtypes = [GP, SP, _D, _D]
+        L.orc_residual.argtypes = [GP, SP, _D, _D, _D]
         L.orc_time_step.argtypes = [GP, SP, _D]
         L.orc_time_step.restype = C.c_double
-        L.orc_rk3_step.argtypes = [GP, SP, _D, C.c_double]
+        L.orc_rk3_step.argtypes = [GP, SP, _D, C.c_double, _D]
         L.orc_rk3_step.restype = C.c_double
-        L.orc_run.argtypes = [GP, SP, _D, C.c_int, C.c_double, C.c_double]
+        L.orc_run.argtypes = [GP, SP, _D, C.c_int, C.c_double, C.c_double, _D]
         L.orc_run.restype = C.c_double
-        L.orc_residual_ext.argtypes = [GP, SP, _D, _D]
+        L.orc_residual_ext.argtypes = [GP, SP, _D, _D, _D]
         L.orc_residual_cells.argtypes = [GP, SP, _D, C.c_long, _L, _D]
         L.orc_residual_cells_ext.argtypes = [GP, SP, _D, C.c_long, _L, _D]
         L.orc_roe_flux.argtypes = [SP, C.c_int, C.c_int, _D, _D, _D]
@@ -95,19 +95,22 @@ def _check(g, U):
     return U
 
 
-def residual(g, U, s: Scheme | None = None) -> np.ndarray:
-    """R_h of Eq. (5) with face areas (S = 0)."""
+def residual(g, U, s: Scheme | None = None, S=None) -> np.ndarray:
+    """R_h of Eq. (5) with face areas; S: cell-averaged source (None: 0)."""
     U = _check(g, U)
     R = np.empty_like(U)
-    lib().orc_residual(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), _ptr(R))
+    S = None if S is None else _check(g, S)
+    lib().orc_residual(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), _ptr(R), None if S is None else _ptr(S))
     return R
 
 
-def residual_ext(g, U, s: Scheme | None = None) -> np.ndarray:
+def residual_ext(g, U, s: Scheme | None = None, S=None) -> np.ndarray:
     """R_h evaluated in extended precision (long double) and rounded to double."""
     U = _check(g, U)
     R = np.empty_like(U)
-    lib().orc_residual_ext(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), _ptr(R))
+    S = None if S is None else _check(g, S)
+    lib().orc_residual_ext(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), _ptr(R),
+                           None if S is None else _ptr(S))
     return R
 
 
@@ -127,17 +130,22 @@ def time_step(g, U, s: Scheme | None = None) -> float:
     return lib().orc_time_step(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U))
 
 
-def rk3_step(g, U, dt: float = 0.0, s: Scheme | None = None):
-    """One SSP-RK3 step; returns (U_new, dt_used)."""
+def rk3_step(g, U, dt: float = 0.0, s: Scheme | None = None, S=None):
+    """One SSP-RK3 step (source S: None for 0); returns (U_new, dt_used)."""
     U = _check(g, U).copy()
-    dt_used = lib().orc_rk3_step(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), dt)
+    S = None if S is None else _check(g, S)
+    dt_used = lib().orc_rk3_step(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), dt,
+                                 None if S is None else _ptr(S))
     return U, dt_used
 
 
-def run(g, U, nsteps: int, dt_fixed: float = 0.0, t_end: float = 0.0, s: Scheme | None = None):
-    """nsteps SSP-RK3 steps (CFL dt unless dt_fixed > 0); returns (U_new, t)."""
+def run(g, U, nsteps: int, dt_fixed: float = 0.0, t_end: float = 0.0, s: Scheme | None = None, S=None):
+    """nsteps SSP-RK3 steps (CFL dt unless dt_fixed > 0; source S: None for 0);
+    returns (U_new, t)."""
     U = _check(g, U).copy()
-    t = lib().orc_run(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), nsteps, dt_fixed, t_end)
+    S = None if S is None else _check(g, S)
+    t = lib().orc_run(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), nsteps, dt_fixed, t_end,
+                      None if S is None else _ptr(S))
     return U, t
 
 
