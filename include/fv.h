@@ -140,10 +140,21 @@ int fv_layout(const fv_ctx *ctx, long long *offsets, int ngrids);
 int fv_set_launch(fv_ctx *ctx, const fv_launch *l);
 int fv_get_launch(const fv_ctx *ctx, fv_launch *l);
 
-/* Spatial residual R_h of Eq. (5): R = sum over faces of F.n ds, face areas
- * included (not divided by |Omega|).  U, R: nvar*ncells doubles (R may not
- * alias U).  rnorm2: NULL, or nvar doubles (device or host) receiving
- * sum over cells of R_v^2 per conserved variable. */
+/* Cell-averaged source S_h of Eq. (5): S is a caller-owned DEVICE array of
+ * nvar*ncells doubles in the layout of U (not copied: it must stay valid and
+ * unchanged while the context uses it), or NULL for S = 0 (the default).
+ * Every later residual, RK step and run includes it: R = sum F.n ds -
+ * |Omega| S, dU/dt = -R/|Omega|.  Waits for the context's queued work and
+ * drops its captured graphs when S changes.  FV_EINVAL for a host pointer,
+ * FV_EUNSUPPORTED for a batched context.  The adjoint is unchanged (S does
+ * not depend on U). */
+int fv_set_source(fv_ctx *ctx, const double *S);
+
+/* Spatial residual R_h of Eq. (5): R = sum over faces of F.n ds - |Omega| S
+ * (S = 0 unless set with fv_set_source), face areas included (not divided by
+ * |Omega|).  U, R: nvar*ncells doubles (R may not alias U).  rnorm2: NULL, or
+ * nvar doubles (device or host) receiving sum over cells of R_v^2 per
+ * conserved variable. */
 int fv_residual(fv_ctx *ctx, const double *U, double *R, double *rnorm2);
 
 /* CFL time step dt = cfl / max over cells of sum_d (|u_d| + c) / dx_d.

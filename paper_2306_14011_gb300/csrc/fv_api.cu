@@ -90,6 +90,7 @@ struct fv_ctx {
   long long norm_part_cap;
   double *X1, *X2;            // adjoint work states (lazy)
   std::vector<GraphEntry> graphs;
+  const double *source;        // caller's cell-averaged source of Eq. (5), or null
   // host-pointer runs: copy-back stream and per-band events (lazy)
   cudaStream_t copy_stream;
   std::vector<cudaEvent_t> band_events;
@@ -203,6 +204,9 @@ int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, dou
   memset(&a, 0, sizeof(a));
   a.tile_begin = tile_begin;
   a.tile_count = tile_count;
+  a.S = c->source;
+  a.vol = 1.0;
+  for (int d = 0; d < g.dim; ++d) a.vol *= g.len[d] / g.n[d];
   a.Us = Us;
   a.Un = Un;
   a.out = out;
@@ -633,6 +637,18 @@ int fv_set_launch(fv_ctx *c, const fv_launch *l) {
   drop_graphs(c);
   if ((r = set_attributes(c))) return r;
   if (c->ngrids > 1) return batch_setup(c);
+  return FV_OK;
+}
+
+int fv_set_source(fv_ctx *c, const double *S) {
+  if (!c) return FV_EINVAL;
+  if (c->ngrids > 1) return FV_EUNSUPPORTED;
+  if (S && !is_device_ptr(S)) return FV_EINVAL;
+  if (S != c->source) {
+    FV_CK(cudaStreamSynchronize(c->stream));  // launches queued with the old source finish first
+    drop_graphs(c);                           // captured graphs hold the old pointer
+    c->source = S;
+  }
   return FV_OK;
 }
 

@@ -97,6 +97,8 @@ __device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double
     a.dt_fixed = b.dt_fixed;
     a.t_acc = nullptr;
     a.flags = b.flags;
+    a.S = nullptr;
+    a.vol = 0.0;
     const int local = item - b.tile_begin[p];
     tile_work<2, MODE>(nullptr, a, local % P.ntile[0], local / P.ntile[0], 0, tile, nullptr, 0u, s_coef, red);
     __syncthreads();  // the next item reuses the shared buffers
@@ -207,7 +209,7 @@ __device__ __forceinline__ void dt_phase(const BatchArgs &b, int slot) {
 
 __global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) batch_run_kernel(const BatchArgs b) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ double s_coef[4];
+  __shared__ double s_coef[5];
   __shared__ double red[4][32];
   double *tile = aligned_smem(smem_raw);
   for (int step = 0; step < b.nsteps; ++step) {

@@ -29,6 +29,8 @@ struct StageArgs {
   int march;           // 3D: 1 = x-y tiles marching along z in chunks of tile[2] planes
   long long tile_begin;  // first tile of this launch (linear tile index, x fastest)
   long long tile_count;  // tiles of this launch (0: all from tile_begin)
+  const double *S;     // cell-averaged source of Eq. (5) (layout of U), or null
+  double vol;          // cell volume |Omega| (with S)
   int limiter;         // FV_LIM_* of Eq. (6)
   double cL, cR;       // unlimited kappa-scheme weights eps (1 -+ kappa) / 4
   double g1;           // gamma - 1

@@ -189,7 +189,7 @@ __device__ __forceinline__ bool sync_timed_out(bool ok, uint64_t *mbar, int firs
 template <int MODE, int LIM>
 __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ double s_coef[4];
+  __shared__ double s_coef[5];
   __shared__ double red[NV3][32];
   const MarchGeom G = march_geom(a.tile);
   double *ring = aligned_smem(smem_raw);
@@ -227,9 +227,10 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
     s_coef[0] = dt;
 #pragma unroll
     for (int d = 0; d < 3; ++d) s_coef[1 + d] = (MODE == MODE_RESIDUAL) ? a.half_ds[d] : -w * dt * a.half_inv_h[d];
+    s_coef[4] = (MODE == MODE_RESIDUAL) ? -a.vol : w * dt;
   }
   __syncthreads();
-  const double dt = s_coef[0], cx = s_coef[1], cy = s_coef[2], cz = s_coef[3];
+  const double dt = s_coef[0], cx = s_coef[1], cy = s_coef[2], cz = s_coef[3], src = s_coef[4];
 
   // ---- prologue: planes z0-2 .. z0+1, the z-face below z0, then plane z0+2
   for (int r = 0; r < kRing; ++r) fetch_plane(&tmap, ring, mbar, r, a, o, ext0, ext1, z0, G);
@@ -288,8 +289,8 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
       for (int v = 0; v < NV3; ++v) {
         // same accumulation as the box-tiled kernel: the stage base, then x, y, z
         const double dFx = Fx[v * G.nfx + fx + 1] - Fx[v * G.nfx + fx];
-        double rv = (MODE == MODE_RESIDUAL) ? cx * dFx
-                                            : fma(cx, dFx, stage_base<MODE>(cur[v * G.plane + lc], a.Un + v * N + gi));
+        double rv = (MODE == MODE_RESIDUAL && !a.S) ? cx * dFx
+                                                    : fma(cx, dFx, start_value<MODE>(a, cur[v * G.plane + lc], v * N + gi, src));
         rv = fma(cy, Fy[v * G.nfy + fy + ext0] - Fy[v * G.nfy + fy], rv);
         rv = fma(cz, Fzc[v * G.cols + c] - Fzp[v * G.cols + c], rv);
         if (MODE == MODE_RESIDUAL && want_norm) nrm[v] = fma(rv, rv, nrm[v]);

@@ -132,10 +132,20 @@ __device__ __forceinline__ double stage_base(double us, const double *un) {
   return fma(1.0 / 3.0, *un, (2.0 / 3.0) * us);
 }
 
+// The value a cell's accumulation starts from: the stage base, plus the
+// source term of Eq. (5) when one is set (src = -|Omega| for the residual,
+// w dt for an RK stage, since dU/dt = -R/|Omega| has +S).
+template <int MODE>
+__device__ __forceinline__ double start_value(const StageArgs &a, double us, long long idx, double src) {
+  double b = stage_base<MODE>(us, a.Un + idx);
+  if (a.S) b = (MODE == MODE_RESIDUAL) ? src * a.S[idx] : fma(src, a.S[idx], b);
+  return b;
+}
+
 template <int DIM, int D, int LIM, int MODE>
 __device__ __forceinline__ void face_pass(const double *__restrict__ tile, double *__restrict__ F,
                                           double *__restrict__ R, const StageArgs &a, const int o[3],
-                                          const int ext[3], const TileGeom &G, double coef) {
+                                          const int ext[3], const TileGeom &G, double coef, double src) {
   constexpr int NV = DIM + 2;
   constexpr int NT = DIM - 1;
   constexpr int E = NV - 1;
@@ -235,7 +245,7 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
     const int flo = (k * fe1 + j) * fe0 + i;
     long long gi = 0;
     int lc = 0;
-    if (D == 0 && MODE != MODE_RESIDUAL) {
+    if (D == 0 && (MODE != MODE_RESIDUAL || a.S)) {
       gi = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
       lc = (((DIM == 3) ? k + 2 : 0) * G.BY + (j + 2)) * G.BX + (i + 2);
     }
@@ -243,10 +253,10 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
     for (int v = 0; v < NV; ++v) {
       const double dF = F[v * G.fmax + flo + fstride] - F[v * G.fmax + flo];
       if (D == 0) {
-        if (MODE == MODE_RESIDUAL)
+        if (MODE == MODE_RESIDUAL && !a.S)
           R[v * G.cells + c] = coef * dF;
         else
-          R[v * G.cells + c] = fma(coef, dF, stage_base<MODE>(tile[v * G.plane + lc], a.Un + v * N + gi));
+          R[v * G.cells + c] = fma(coef, dF, start_value<MODE>(a, tile[v * G.plane + lc], v * N + gi, src));
       } else {
         R[v * G.cells + c] = fma(coef, dF, R[v * G.cells + c]);
       }
@@ -258,7 +268,8 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
 // All the work of one tile: stage the tile (TMA with mbarrier `bar` at parity
 // `phase`, or plain loads), compute the face fluxes axis by axis, accumulate
 // the residual (or the new stage state) and write it.  `tile` is the CTA's dynamic shared
-// memory (128-byte aligned); s_coef and red are static shared scratch.
+// memory (128-byte aligned); s_coef (5 doubles) and red are static shared
+// scratch.
 // Returns false (uniformly across the CTA) if the tile load timed out.
 template <int DIM, int MODE, int LIM = FV_LIM_MINMOD>
 __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageArgs &a, int bx, int by, int bz,
@@ -321,12 +332,13 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
     s_coef[0] = dt;
 #pragma unroll
     for (int d = 0; d < 3; ++d) s_coef[1 + d] = (MODE == MODE_RESIDUAL) ? a.half_ds[d] : -w * dt * a.half_inv_h[d];
+    s_coef[4] = (MODE == MODE_RESIDUAL) ? -a.vol : w * dt;
   }
   __syncthreads();
   const double dt = s_coef[0];
-  face_pass<DIM, 0, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[1]);
-  face_pass<DIM, 1, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[2]);
-  if constexpr (DIM == 3) face_pass<DIM, 2, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[3]);
+  face_pass<DIM, 0, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[1], s_coef[4]);
+  face_pass<DIM, 1, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[2], s_coef[4]);
+  if constexpr (DIM == 3) face_pass<DIM, 2, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[3], s_coef[4]);
 
   // ---- 4. epilogue
   const int ncell = ext[0] * ext[1] * ext[2];
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(DIM == 2 ? 256 : kStage3dMaxThreads, FV_STAGE_
     stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
   constexpr int NV = DIM + 2;
   extern __shared__ unsigned char smem_raw[];
-  __shared__ double s_coef[4];
+  __shared__ double s_coef[5];
   __shared__ double red[NV][32];
   double *tile = aligned_smem(smem_raw);
   uint64_t *mbar = stage_mbar<DIM>(tile, a);

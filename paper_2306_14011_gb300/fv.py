@@ -110,6 +110,8 @@ def load() -> C.CDLL:
         L.fv_tune.restype = C.c_int
         L.fv_tune_space.argtypes = [C.c_int, P(C.c_int), P(C.c_double)]
         L.fv_tune_space.restype = C.c_int
+        L.fv_set_source.argtypes = [_VP, _VP]
+        L.fv_set_source.restype = C.c_int
         L.fv_debug_wait.argtypes = [C.c_int, C.c_double, _VP]
         L.fv_debug_wait.restype = C.c_int
         L.fv_debug_bits.argtypes = [C.c_int, _VP, _VP, _VP, C.c_long, _VP]
@@ -342,6 +344,12 @@ def fv_tune_space(dim: int):
     return n.value, size.value
 
 
+def fv_set_source(ctx: int, S):
+    """Cell-averaged source of Eq. (5): a device array shaped like the state, or
+    None for S = 0 (the caller keeps S alive while the context uses it)."""
+    _check(load().fv_set_source(ctx, None if S is None else _ptr(S)), "fv_set_source")
+
+
 def fv_debug_wait(kind: int, limit_seconds: float, stream=None):
     """Run one of the library's bounded device waits on something that never
     completes (kind 0: the tile-load mbarrier wait, 1: the grid-barrier spin);
@@ -460,6 +468,16 @@ class Solver:
         out = torch_empty_like(U) if out is None else out
         fv_adjoint_vjp(self.ctx, FV_VJP_RKSTEP, U, lam, dt, out)
         return out
+
+    def set_source(self, S):
+        """Cell-averaged source S_h of Eq. (5) (a device tensor shaped like the
+        state, kept referenced here), or None for S = 0."""
+        if S is not None:
+            self._chk(S)
+            if not S.is_contiguous() or not S.is_cuda:
+                raise ValueError("the source must be a contiguous CUDA tensor")
+        fv_set_source(self.ctx, S)
+        self._source = S
 
     def tune(self, U, **opts):
         """Run the autotuner on state U; installs and returns the tuned launch."""
