@@ -46,7 +46,32 @@ struct Scheme {
   double kappa;  // MUSCL kappa of Eq. (6): -1 -> fully upwind
   double efix;   // Harten entropy-fix width as a fraction of the Roe sound speed
   int limiter;   // Psi of Eq. (6): LIM_MINMOD, LIM_VANLEER or LIM_NONE (Psi = 1)
+  int recon;     // variables Eq. (6) extrapolates: RECON_CONSERVED (Sec. 3.1) or RECON_PRIMITIVE
 };
+enum { RECON_CONSERVED = 0, RECON_PRIMITIVE = 1 };
+
+// Primitive variables (rho, u_1..u_dim, p) of a conserved state
+// (rho, m_1..m_dim, E), and back: u = m / rho, p = (gamma-1)(E - rho |u|^2 / 2).
+template <class T>
+void to_primitive(const Scheme &s, int dim, const T *q, T *w) {
+  w[0] = q[0];
+  T q2 = T(0.0);
+  for (int a = 0; a < dim; ++a) {
+    w[1 + a] = q[1 + a] / q[0];
+    q2 = q2 + w[1 + a] * w[1 + a];
+  }
+  w[dim + 1] = (s.gamma - 1.0) * (q[dim + 1] - 0.5 * q[0] * q2);
+}
+template <class T>
+void to_conserved(const Scheme &s, int dim, const T *w, T *q) {
+  q[0] = w[0];
+  T q2 = T(0.0);
+  for (int a = 0; a < dim; ++a) {
+    q[1 + a] = w[0] * w[1 + a];
+    q2 = q2 + w[1 + a] * w[1 + a];
+  }
+  q[dim + 1] = w[dim + 1] / (s.gamma - 1.0) + 0.5 * w[0] * q2;
+}
 
 // ---------------------------------------------------------------- scalar helpers
 inline double value(double x) { return x; }
@@ -301,12 +326,23 @@ void residual(const Grid &g, const Scheme &s, const T *U, T *R, const double *S 
       // the cells left of the face: (i,j,k) - e_d
       int a = i - e[0], b = j - e[1], c = k - e[2];
       T QL[5], QR[5], Ff[5];
+      T q[4][5];  // the stencil Q_{k-1}, Q_k, Q_{k+1}, Q_{k+2}
       for (int v = 0; v < nv; ++v) {
-        T q0 = P[L.pidx(v, a - e[0], b - e[1], c - e[2])];  // Q_{k-1}
-        T q1 = P[L.pidx(v, a, b, c)];                       // Q_k
-        T q2 = P[L.pidx(v, i, j, k)];                       // Q_{k+1}
-        T q3 = P[L.pidx(v, i + e[0], j + e[1], k + e[2])];  // Q_{k+2}
-        muscl(s, q0, q1, q2, q3, QL[v], QR[v]);
+        q[0][v] = P[L.pidx(v, a - e[0], b - e[1], c - e[2])];
+        q[1][v] = P[L.pidx(v, a, b, c)];
+        q[2][v] = P[L.pidx(v, i, j, k)];
+        q[3][v] = P[L.pidx(v, i + e[0], j + e[1], k + e[2])];
+      }
+      if (s.recon == RECON_PRIMITIVE) {
+        // Eq. (6) applied to the primitive variables, the face states then
+        // converted back to conserved variables for the flux
+        T w[4][5], WL[5], WR[5];
+        for (int m = 0; m < 4; ++m) to_primitive(s, L.dim, q[m], w[m]);
+        for (int v = 0; v < nv; ++v) muscl(s, w[0][v], w[1][v], w[2][v], w[3][v], WL[v], WR[v]);
+        to_conserved(s, L.dim, WL, QL);
+        to_conserved(s, L.dim, WR, QR);
+      } else {
+        for (int v = 0; v < nv; ++v) muscl(s, q[0][v], q[1][v], q[2][v], q[3][v], QL[v], QR[v]);
       }
       roe_flux(s, L.dim, d, QL, QR, Ff);
       for (int v = 0; v < nv; ++v) F[(size_t)v * nface + f] = Ff[v];

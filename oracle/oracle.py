@@ -23,13 +23,17 @@ class Grid(C.Structure):
 LIM_MINMOD, LIM_VANLEER, LIM_NONE = 0, 1, 2
 
 
+RECON_CONSERVED, RECON_PRIMITIVE = 0, 1
+
+
 class Scheme(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("eps", C.c_double), ("kappa", C.c_double),
-                ("efix", C.c_double), ("limiter", C.c_int)]
+                ("efix", C.c_double), ("limiter", C.c_int), ("recon", C.c_int)]
 
 
-def scheme(gamma=GAMMA, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, limiter=LIM_MINMOD) -> Scheme:
-    return Scheme(gamma, cfl, eps, kappa, efix, limiter)
+def scheme(gamma=GAMMA, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, limiter=LIM_MINMOD,
+           recon=RECON_CONSERVED) -> Scheme:
+    return Scheme(gamma, cfl, eps, kappa, efix, limiter, recon)
 
 
 _lib = None
