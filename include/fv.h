@@ -62,6 +62,7 @@ typedef struct fv_grid {
 } fv_grid;
 
 enum { FV_LIM_MINMOD = 0, FV_LIM_VANLEER = 1, FV_LIM_NONE = 2 };
+enum { FV_RECON_CONSERVED = 0, FV_RECON_PRIMITIVE = 1 };
 
 /* gamma: ratio of specific heats (1.4).  cfl: CFL number (0.5).
  * eps, kappa: MUSCL parameters of Eq. (6); eps = 1 gives second order.
@@ -72,10 +73,16 @@ enum { FV_LIM_MINMOD = 0, FV_LIM_VANLEER = 1, FV_LIM_NONE = 2 };
  * slopes are equal, so kappa matters only for FV_LIM_NONE.  Batched contexts
  * and the adjoint support FV_LIM_MINMOD only.
  * efix: Harten entropy-fix width as a fraction of the Roe sound speed (0.1);
- * 0 disables the fix. */
+ * 0 disables the fix.
+ * recon: the variables Eq. (6) extrapolates -- FV_RECON_CONSERVED (Sec. 3.1,
+ * the default) or FV_RECON_PRIMITIVE (rho, velocity, p; the face states are
+ * converted back to conserved variables for the flux).  Primitive
+ * reconstruction is not supported by batched contexts, the adjoint or the
+ * z-marching kernel (launch field march). */
 typedef struct fv_scheme {
   double gamma, cfl, eps, kappa, efix;
   int limiter;
+  int recon;
 } fv_scheme;
 
 enum { FV_LOADER_TMA = 0, FV_LOADER_PLAIN = 1 };

@@ -134,13 +134,15 @@ int validate_scheme(const fv_scheme *s) {
   if (!s || !(s->gamma > 1.0) || !(s->cfl > 0.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0))
     return FV_EINVAL;
   if (s->limiter != FV_LIM_MINMOD && s->limiter != FV_LIM_VANLEER && s->limiter != FV_LIM_NONE) return FV_EINVAL;
+  if (s->recon != FV_RECON_CONSERVED && s->recon != FV_RECON_PRIMITIVE) return FV_EINVAL;
   return FV_OK;
 }
 
-int validate_launch(const fv_grid *g, const fv_launch *l, size_t smem_optin) {
+int validate_launch(const fv_grid *g, const fv_scheme *sch, const fv_launch *l, size_t smem_optin) {
   for (int s = 0; s < 3; ++s) {
     const fv_kernel_cfg &k = l->stage[s];
     if (k.march != 0 && (k.march != 1 || g->dim != 3)) return FV_EINVAL;
+    if (k.march && sch->recon != FV_RECON_CONSERVED) return FV_EINVAL;  // z-marching: conserved only
     for (int d = 0; d < 3; ++d) {
       if (d == 2 && k.march) {
         if (k.tile[2] < 1 || k.tile[2] > (1 << 24)) return FV_EINVAL;  // planes per chunk
@@ -228,6 +230,8 @@ int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, dou
     a.half_inv_h[d] = 0.5 / h[d];
   }
   a.limiter = c->scheme.limiter;
+  a.recon = c->scheme.recon;
+  a.inv_g1 = 1.0 / (c->scheme.gamma - 1.0);
   a.cL = 0.25 * c->scheme.eps * (1.0 - c->scheme.kappa);
   a.cR = 0.25 * c->scheme.eps * (1.0 + c->scheme.kappa);
   a.g1 = c->scheme.gamma - 1.0;
@@ -487,7 +491,7 @@ int ctx_work_state(fv_ctx *c, const double *U, double **Uw) {
 }
 
 int ctx_time_launch(fv_ctx *c, double *Uw, const fv_launch *l, int steps, int repeats, double *sec) {
-  int r = validate_launch(&c->grid, l, c->smem_optin);
+  int r = validate_launch(&c->grid, &c->scheme, l, c->smem_optin);
   if (r) return r;
   const fv_launch saved = c->launch;
   c->launch = *l;
@@ -517,7 +521,9 @@ int ctx_time_launch(fv_ctx *c, double *Uw, const fv_launch *l, int steps, int re
 }
 
 int ctx_sm_count(const fv_ctx *c) { return c->sms; }
-int ctx_validate_launch(const fv_ctx *c, const fv_launch *l) { return validate_launch(&c->grid, l, c->smem_optin); }
+int ctx_validate_launch(const fv_ctx *c, const fv_launch *l) {
+  return validate_launch(&c->grid, &c->scheme, l, c->smem_optin);
+}
 int ctx_default_launch(const fv_ctx *c, fv_launch *l) { return fv_default_launch(&c->grid, l); }
 int ctx_dim(const fv_ctx *c) { return c->grid.dim; }
 
@@ -581,7 +587,7 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
     fv_destroy(c);
     return code;
   };
-  if (ngrids > 1 && s->limiter != FV_LIM_MINMOD) return fail(FV_EUNSUPPORTED);
+  if (ngrids > 1 && (s->limiter != FV_LIM_MINMOD || s->recon != FV_RECON_CONSERVED)) return fail(FV_EUNSUPPORTED);
   if (ngrids > 1 && (r = batch_init(c, grids, ngrids))) return fail(r);
   if (cudaGetDevice(&c->device) != cudaSuccess) return fail(cuda_fail(cudaErrorNoDevice));
   cudaDeviceProp prop;
@@ -598,7 +604,7 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
     if (ngrids > 1)
       for (int s = 0; s < 3; ++s) c->launch.stage[s].threads = 256;
   }
-  if ((r = validate_launch(&c->grid, &c->launch, c->smem_optin))) return fail(r);
+  if ((r = validate_launch(&c->grid, &c->scheme, &c->launch, c->smem_optin))) return fail(r);
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(FV_ECUDA);
   if (cudaMalloc(&c->U1, c->state_bytes) != cudaSuccess || cudaMalloc(&c->U2, c->state_bytes) != cudaSuccess)
     return fail(cuda_fail(cudaErrorMemoryAllocation));
@@ -631,7 +637,7 @@ int fv_layout(const fv_ctx *c, long long *offsets, int ngrids) {
 
 int fv_set_launch(fv_ctx *c, const fv_launch *l) {
   if (!c || !l) return FV_EINVAL;
-  int r = validate_launch(&c->grid, l, c->smem_optin);
+  int r = validate_launch(&c->grid, &c->scheme, l, c->smem_optin);
   if (r) return r;
   c->launch = *l;
   drop_graphs(c);
@@ -929,7 +935,8 @@ int adjoint(fv_ctx *c, const double *U, const double *lam, double *out, double w
 
 extern "C" int fv_adjoint_vjp(fv_ctx *c, int what, const double *U, const double *lam, double dt, double *out) {
   if (!c || !U || !lam || !out || out == U || out == lam) return FV_EINVAL;
-  if (c->ngrids > 1 || c->scheme.limiter != FV_LIM_MINMOD) return FV_EUNSUPPORTED;
+  if (c->ngrids > 1 || c->scheme.limiter != FV_LIM_MINMOD || c->scheme.recon != FV_RECON_CONSERVED)
+    return FV_EUNSUPPORTED;
   if (!is_device_ptr(U) || !is_device_ptr(lam) || !is_device_ptr(out)) return FV_EINVAL;
   if (what == FV_VJP_RESIDUAL) return adjoint(c, U, lam, out, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0);
   if (what != FV_VJP_RKSTEP || !(dt > 0.0)) return FV_EINVAL;

@@ -87,6 +87,7 @@ __device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double
     }
     a.use_tma = 0;
     a.limiter = FV_LIM_MINMOD;
+    a.recon = FV_RECON_CONSERVED;
     a.cL = a.cR = 0.0;
     a.g1 = b.g1;
     a.half_eps = b.half_eps;

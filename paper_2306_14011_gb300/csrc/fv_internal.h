@@ -32,6 +32,8 @@ struct StageArgs {
   const double *S;     // cell-averaged source of Eq. (5) (layout of U), or null
   double vol;          // cell volume |Omega| (with S)
   int limiter;         // FV_LIM_* of Eq. (6)
+  int recon;           // FV_RECON_*: the variables Eq. (6) extrapolates
+  double inv_g1;       // 1 / (gamma - 1) (primitive reconstruction)
   double cL, cR;       // unlimited kappa-scheme weights eps (1 -+ kappa) / 4
   double g1;           // gamma - 1
   double half_eps;     // eps / 2 (MUSCL slope weight)

@@ -89,7 +89,8 @@ bool grid_ok(const fv_grid *g) {
 extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const double *U, double *R,
                                    double *rnorm2, void *stream) {
   if (!grid_ok(g) || !s || !(s->gamma > 1.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0) ||
-      s->limiter < FV_LIM_MINMOD || s->limiter > FV_LIM_NONE)
+      s->limiter < FV_LIM_MINMOD || s->limiter > FV_LIM_NONE ||
+      (s->recon != FV_RECON_CONSERVED && s->recon != FV_RECON_PRIMITIVE))
     return FV_EINVAL;
   if (!U || !R || U == R || !device_pointer(U) || !device_pointer(R) || (rnorm2 && !device_pointer(rnorm2)))
     return FV_EINVAL;
@@ -142,6 +143,8 @@ extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const d
   a.use_tma = 0;  // plain loads: no tensor map, results identical to the TMA loader
   a.march = k.march;
   a.limiter = s->limiter;
+  a.recon = s->recon;
+  a.inv_g1 = 1.0 / (s->gamma - 1.0);
   a.cL = 0.25 * s->eps * (1.0 - s->kappa);
   a.cR = 0.25 * s->eps * (1.0 + s->kappa);
   a.g1 = s->gamma - 1.0;

@@ -122,6 +122,39 @@ __device__ __forceinline__ void muscl_states(double q0, double q1, double q2, do
   muscl_from_diffs<LIM>(q1, q2, q1 - q0, q2 - q1, q3 - q2, h, cL, cR, QL, QR);
 }
 
+// Conserved state (rho, m, E) of primitive variables (rho, u, p), in place:
+// m = rho u, E = p / (gamma - 1) + rho |u|^2 / 2.
+template <int DIM>
+__device__ __forceinline__ void to_conserved(double (&w)[DIM + 2], double inv_g1) {
+  double q2 = w[1] * w[1];
+#pragma unroll
+  for (int d = 1; d < DIM; ++d) q2 = fma(w[1 + d], w[1 + d], q2);
+  const double e = fma(scale_pow2<-1>(w[0]), q2, w[DIM + 1] * inv_g1);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) w[1 + d] = w[0] * w[1 + d];
+  w[DIM + 1] = e;
+}
+
+// Every cell of the staged box from conserved to primitive variables, in
+// place: u = m / rho, p = (gamma - 1)(E - m.u / 2).  Corner cells the stencils
+// never read may hold zeros; whatever they turn into is never used.
+template <int DIM>
+__device__ __forceinline__ void box_to_primitive(double *tile, const TileGeom &G, double g1) {
+  for (int c = threadIdx.x; c < G.plane; c += blockDim.x) {
+    const double rho = tile[c];
+    const double r = rcp_fp64(rho);
+    double k = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const double m = tile[(1 + d) * G.plane + c];
+      const double u = m * r;
+      k = (d == 0) ? m * u : fma(m, u, k);
+      tile[(1 + d) * G.plane + c] = u;
+    }
+    tile[(DIM + 1) * G.plane + c] = g1 * fma(-0.5, k, tile[(DIM + 1) * G.plane + c]);
+  }
+}
+
 // The part of a stage update that does not depend on the fluxes: Us (stage
 // 1), 3/4 Un + 1/4 Us (stage 2), 1/3 Un + 2/3 Us (stage 3); 0 for the residual.
 template <int MODE>
@@ -201,6 +234,10 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
         dm[v] = d0[v];
         d0[v] = dp;
       }
+      if (a.recon == FV_RECON_PRIMITIVE) {  // (rho, u, p) face states -> (rho, m, E)
+        to_conserved<DIM>(QL, a.inv_g1);
+        to_conserved<DIM>(QR, a.inv_g1);
+      }
       // normal-first ordering: (rho, m_D, tangential momenta, E)
       double qL[NT + 3], qR[NT + 3], Gf[NT + 3];
       qL[0] = QL[0];
@@ -256,7 +293,9 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
         if (MODE == MODE_RESIDUAL && !a.S)
           R[v * G.cells + c] = coef * dF;
         else
-          R[v * G.cells + c] = fma(coef, dF, start_value<MODE>(a, tile[v * G.plane + lc], v * N + gi, src));
+          R[v * G.cells + c] =
+              fma(coef, dF, start_value<MODE>(a, a.recon == FV_RECON_PRIMITIVE ? a.Us[v * N + gi] : tile[v * G.plane + lc],
+                                              v * N + gi, src));
       } else {
         R[v * G.cells + c] = fma(coef, dF, R[v * G.cells + c]);
       }
@@ -335,6 +374,10 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
     s_coef[4] = (MODE == MODE_RESIDUAL) ? -a.vol : w * dt;
   }
   __syncthreads();
+  if (a.recon == FV_RECON_PRIMITIVE) {  // Eq. (6) on (rho, u, p)
+    box_to_primitive<DIM>(tile, G, a.g1);
+    __syncthreads();
+  }
   const double dt = s_coef[0];
   face_pass<DIM, 0, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[1], s_coef[4]);
   face_pass<DIM, 1, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[2], s_coef[4]);

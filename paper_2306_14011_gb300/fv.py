@@ -37,11 +37,12 @@ class fv_grid(C.Structure):
 
 
 FV_LIM_MINMOD, FV_LIM_VANLEER, FV_LIM_NONE = 0, 1, 2
+FV_RECON_CONSERVED, FV_RECON_PRIMITIVE = 0, 1
 
 
 class fv_scheme(C.Structure):
     _fields_ = [("gamma", C.c_double), ("cfl", C.c_double), ("eps", C.c_double), ("kappa", C.c_double),
-                ("efix", C.c_double), ("limiter", C.c_int)]
+                ("efix", C.c_double), ("limiter", C.c_int), ("recon", C.c_int)]
 
 
 class fv_kernel_cfg(C.Structure):
@@ -152,8 +153,9 @@ def make_grid(g) -> fv_grid:
     return G
 
 
-def make_scheme(gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, limiter=FV_LIM_MINMOD) -> fv_scheme:
-    return fv_scheme(gamma, cfl, eps, kappa, efix, limiter)
+def make_scheme(gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, limiter=FV_LIM_MINMOD,
+                recon=FV_RECON_CONSERVED) -> fv_scheme:
+    return fv_scheme(gamma, cfl, eps, kappa, efix, limiter, recon)
 
 
 def launch_to_dict(l: fv_launch) -> dict:
@@ -388,16 +390,17 @@ class Solver:
 
     Solver(grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1,
            launch=None (dict or fv_launch), stream=None (torch's current stream),
-           limiter=FV_LIM_MINMOD | FV_LIM_VANLEER | FV_LIM_NONE)
+           limiter=FV_LIM_MINMOD | FV_LIM_VANLEER | FV_LIM_NONE,
+           recon=FV_RECON_CONSERVED | FV_RECON_PRIMITIVE)
     """
 
     def __init__(self, grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, launch=None, stream=None,
-                 limiter=FV_LIM_MINMOD):
+                 limiter=FV_LIM_MINMOD, recon=FV_RECON_CONSERVED):
         self.batched = isinstance(grid, (list, tuple))
         self.grids = list(grid) if self.batched else [grid]
         self.grid = self.grids[0]
         self.ngrids = len(self.grids)
-        self.scheme = make_scheme(gamma, cfl, eps, kappa, efix, limiter)
+        self.scheme = make_scheme(gamma, cfl, eps, kappa, efix, limiter, recon)
         if isinstance(launch, dict):
             launch = launch_from_dict(launch)
         self.ctx = fv_init(grid, self.scheme, launch, stream)
