@@ -99,7 +99,8 @@ enum { FV_LOADER_TMA = 0, FV_LOADER_PLAIN = 1 };
  * 1 = x-y tiles of tile[0] x tile[1] columns that march along z through
  * chunks of tile[2] planes (1..nz), computing every z-face once per chunk.
  * Time-step reduction: threads per CTA (32..1024) and grid = number of CTAs
- * (0 = two per SM); tile, loader and march are ignored. */
+ * (0 = 2048 / threads per SM, filling every SM); tile, loader and march are
+ * ignored. */
 typedef struct fv_kernel_cfg {
   int tile[3];
   int threads;
@@ -119,7 +120,7 @@ typedef struct fv_ctx fv_ctx;
 /* Fill *l with the default launch configuration for grid g (one tile shape
  * and thread count for all stages): 2D 32x32 box tiles with 160 threads (256
  * in a batched context created without a launch); 3D
- * 8x8x8 box tiles with 192 threads; time-step reduction 512 threads, two
+ * 8x8x8 box tiles with 192 threads; time-step reduction 512 threads, four
  * CTAs per SM.  Returns FV_EINVAL for a bad grid. */
 int fv_default_launch(const fv_grid *g, fv_launch *l);
 

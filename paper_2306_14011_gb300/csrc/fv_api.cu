@@ -82,6 +82,7 @@ struct fv_ctx {
   double *stage_in, *stage_out;  // host-pointer staging (lazy)
   unsigned long long *smax;   // scratch: bits of the max wave-speed sum
   unsigned *lbound;           // scratch: bits of its certified FP32 lower bound
+  unsigned *chunk_hi;         // per 32-cell chunk: bits of its certified upper bound
   unsigned *flags;            // scratch: device flags
   double *t_acc;              // scratch: simulated time
   double *dt_dev;             // scratch: dt for device outputs
@@ -268,10 +269,13 @@ int dt_launch(fv_ctx *c, const double *U, cudaStream_t st) {
   for (int d = 0; d < c->grid.dim; ++d) b = b && a.inv_h[d] >= 0x1p-30 && a.inv_h[d] <= 0x1p30;
   a.bounded = b ? 1 : 0;
   a.lbound = c->lbound;
+  a.chunk_hi = c->chunk_hi;
   a.g1f = (float)a.g1;
   a.gammaf = (float)a.gamma;
   for (int d = 0; d < 3; ++d) a.inv_hf[d] = (float)a.inv_h[d];
-  int blocks = c->launch.dt.grid > 0 ? c->launch.dt.grid : 2 * c->sms;
+  // grid 0: enough CTAs to fill every SM with 2048 threads (both passes read
+  // the state from HBM and need loads in flight)
+  int blocks = c->launch.dt.grid > 0 ? c->launch.dt.grid : std::max(1, 2048 / c->launch.dt.threads) * c->sms;
   const long long need = (c->ncells + c->launch.dt.threads - 1) / c->launch.dt.threads;
   if (blocks > need) blocks = (int)(need > 0 ? need : 1);
   FV_CK(cudaMemsetAsync(c->smax, 0, 16, st));  // smax and the FP32 bound
@@ -618,6 +622,8 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
   c->dt_dev = reinterpret_cast<double *>(scr + 32);
   c->norm_out = reinterpret_cast<double *>(scr + 40);
   if (cudaMemset(scr, 0, 256) != cudaSuccess) return fail(FV_ECUDA);
+  if (cudaMalloc(&c->chunk_hi, sizeof(unsigned) * (size_t)((c->ncells + 31) / 32)) != cudaSuccess)
+    return fail(cuda_fail(cudaErrorMemoryAllocation));
   if ((r = set_attributes(c))) return fail(r);
   if (c->ngrids > 1 && (r = batch_setup(c))) return fail(r);
   *out = c;
@@ -967,6 +973,7 @@ void fv_destroy(fv_ctx *c) {
   if (c->U2) cudaFree(c->U2);
   if (c->stage_in) cudaFree(c->stage_in);
   if (c->stage_out) cudaFree(c->stage_out);
+  if (c->chunk_hi) cudaFree(c->chunk_hi);
   for (cudaEvent_t e : c->band_events) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->smax) cudaFree(c->smax);  // start of the scratch block

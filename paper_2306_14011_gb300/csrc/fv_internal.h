@@ -61,6 +61,7 @@ struct DtArgs {
   // evaluates in FP64 only the cells whose certified upper bound reaches it
   int bounded;
   unsigned *lbound;
+  unsigned *chunk_hi;  // per 32-cell chunk: bits of its certified FP32 upper bound
   float g1f, gammaf, inv_hf[3];
 };
 

@@ -29,23 +29,39 @@ cudaError_t stage_kernel_attributes(int dim, size_t smem) {
   return e == cudaSuccess ? set_march_attributes(smem) : e;
 }
 
+// Cells are handled in chunks of 32 consecutive cells, one warp per chunk
+// (the same chunks in both passes, whatever the launch shape).
+constexpr int kDtChunk = 32;
+
 // Pass 1: the largest certified lower bound s32 (1 - rel), rounded down, over
-// all cells (atomicMax on the bits of a non-negative float).
+// all cells (atomicMax on the bits of a non-negative float), and per chunk the
+// largest certified upper bound s32 (1 + rel), rounded up (+inf when a cell of
+// the chunk is not certified).
 template <int DIM>
 __global__ void __launch_bounds__(1024) dt_bound_kernel(const DtArgs a) {
   const long long N = a.ncells;
+  const long long nchunk = (N + kDtChunk - 1) / kDtChunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
   unsigned best = 0u;
-#pragma unroll 4
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-    float s32, rel;
-    if (wave_sum32<DIM>(a.U, a.ncells, c, a.g1f, a.gammaf, a.inv_hf, s32, rel)) {
-      const unsigned lo = __float_as_uint(__fmul_rd(s32, __fsub_rd(1.0f, rel)));
-      best = lo > best ? lo : best;
+  for (long long ch = (long long)blockIdx.x * (blockDim.x >> 5) + warp; ch < nchunk; ch += wstride) {
+    const long long c = ch * kDtChunk + lane;
+    unsigned hi = 0u;
+    if (c < N) {
+      float s32, rel;
+      if (wave_sum32<DIM>(a.U, N, c, a.g1f, a.gammaf, a.inv_hf, s32, rel)) {
+        const unsigned lo = __float_as_uint(__fmul_rd(s32, __fsub_rd(1.0f, rel)));
+        best = lo > best ? lo : best;
+        hi = __float_as_uint(__fmul_ru(s32, __fadd_ru(1.0f, rel)));
+      } else {
+        hi = 0x7f800000u;  // +inf: the chunk must be evaluated
+      }
     }
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) a.chunk_hi[ch] = hi;
   }
   best = __reduce_max_sync(0xffffffffu, best);
   __shared__ unsigned wmax[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) wmax[warp] = best;
   __syncthreads();
   if (warp == 0) {
@@ -60,26 +76,25 @@ __global__ void __launch_bounds__(1024) dt_bound_kernel(const DtArgs a) {
 // (max of non-negative doubles = max of their bit patterns): per thread, warp
 // shuffle, CTA, then one atomicMax per CTA.  Cells with rho <= 0, p <= 0 or
 // NaN raise FLAG_NONPHYSICAL and are left out.  With the pre-selection, a
-// cell whose certified upper bound s32 (1 + rel) (rounded up) is below the
-// certified lower bound L of pass 1 cannot hold the maximum and is skipped;
-// uncertified cells are always evaluated.  The cell attaining the maximum is
-// never skipped (its upper bound is at least its sum, which is at least L),
-// so the result is the exact FP64 maximum.
+// chunk whose certified upper bound is below the certified lower bound L of
+// pass 1 cannot hold the maximum and is skipped without reading it; chunks
+// with an uncertified cell are always evaluated.  The chunk holding the
+// maximum is never skipped (its upper bound is at least the maximum, which
+// is at least L), so the result is the exact FP64 maximum.
 template <int DIM>
 __global__ void __launch_bounds__(1024) dt_kernel(const DtArgs a) {
   constexpr int NV = DIM + 2;
   const long long N = a.ncells;
-  const float L = a.bounded ? __uint_as_float(*a.lbound) : 0.0f;
+  const long long nchunk = (N + kDtChunk - 1) / kDtChunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+  const unsigned L = a.bounded ? *a.lbound : 0u;
   unsigned long long best = 0ull;
   bool bad = false;
-#pragma unroll 4
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-    if (a.bounded) {
-      float s32, rel;
-      if (wave_sum32<DIM>(a.U, a.ncells, c, a.g1f, a.gammaf, a.inv_hf, s32, rel) &&
-          __fmul_ru(s32, __fadd_ru(1.0f, rel)) < L)
-        continue;
-    }
+  for (long long ch = (long long)blockIdx.x * (blockDim.x >> 5) + warp; ch < nchunk; ch += wstride) {
+    if (a.bounded && a.chunk_hi[ch] < L) continue;  // non-negative float bits order like the values
+    const long long c = ch * kDtChunk + lane;
+    if (c >= N) continue;
     const double rho = a.U[c];
     if (not_positive_finite(rho)) {
       bad = true;
@@ -114,7 +129,6 @@ __global__ void __launch_bounds__(1024) dt_kernel(const DtArgs a) {
     best = o > best ? o : best;
   }
   __shared__ unsigned long long wmax[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) wmax[warp] = best;
   const int anybad = __syncthreads_or(bad);
   if (warp == 0) {

@@ -130,7 +130,7 @@ bool cfg_of(const Space &sp, const fv_launch &l, int sms, Cfg *out) {
   }
   const int b = 3 * sp.per_stage;
   if (!find(b, l.dt.threads)) return false;
-  const int mult = l.dt.grid == 0 ? 2 : l.dt.grid / sms;
+  const int mult = l.dt.grid == 0 ? std::max(1, 2048 / l.dt.threads) : l.dt.grid / sms;  // grid 0: SMs filled
   if (l.dt.grid != 0 && l.dt.grid % sms) return false;
   if (!find(b + 1, mult)) return false;
   *out = c;
