@@ -171,7 +171,10 @@ def run_ours(args):
     W = make_workload(args, I)
     g, U0 = W["grid"], W["U0"]
     cells = W["cells"]
-    solver = fv.Solver(g, stream=stream)
+    split = args.mode == "split"
+    if split and W["batched"]:
+        raise SystemExit("--mode split: batched contexts run the fused persistent kernel only")
+    solver = fv.Solver(g, stream=stream, mode=fv.FV_SPLIT if split else None)
     U = torch.from_numpy(U0).to(dev) if not W["batched"] else solver.pack(
         [torch.from_numpy(u).to(dev) for u in W["states"]])
     if W["batched"]:
@@ -245,7 +248,7 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs")
     achieved_gbs = W["bytes"] * cells / (stage_ms / 1e3) / 1e9
     st0 = solver.launch["stage"][0]
-    traffic = STAGE_TRAFFIC["bytes"] if (STAGE_TRAFFIC["source_hash"] == kernel_source_hash() and
+    traffic = STAGE_TRAFFIC["bytes"] if (not split and STAGE_TRAFFIC["source_hash"] == kernel_source_hash() and
                                          list(st0["tile"]) == STAGE_TRAFFIC["tile"] and
                                          st0["threads"] == STAGE_TRAFFIC["threads"]) else None
     line = {
@@ -262,18 +265,23 @@ def run_ours(args):
         "dtype": "f64",
         "data": "synthetic (seeded Kelvin-Helmholtz initial condition)",
         "config": {"workload": W["desc"], "cells": cells, "launch": "default", "launch_params": solver.launch,
+                   "kernel_structure": ("split: per stage %d kernels (limiter and flux per axis, source, RHS, "
+                                        "update; Sec. 3.4), intermediates in HBM" % (2 * g.dim + 3)) if split
+                   else "fused: one kernel per RK stage",
                    "l2": "state (%.0f MB) larger than L2, no flush" % (U0.nbytes / 1e6),
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic if W["name"] == "kh4096" else None,
-                     "kernel": W["kernel"], "stage_ms": stage_ms, "dt_kernel_ms": dt_ms,
+                     "kernel": ("all %d split kernels of one stage (per-kernel times: profiles)" % (2 * g.dim + 3))
+                     if split else W["kernel"], "stage_ms": stage_ms, "dt_kernel_ms": dt_ms,
                      "flop_per_cell_stage": W["flop"],
                      "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz",
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm_peak,
                      "hbm_frac": (achieved_gbs / hbm_peak) if hbm_peak else None,
                      "bytes_per_cell_stage": W["bytes"]},
         "e2e": e2e,
-        "gpu_launches": W["launches_per_step"] * args.steps if not W["batched"] else 1,
+        "gpu_launches": ((2 + 3 * (2 * g.dim + 3)) if split else W["launches_per_step"]) * args.steps
+        if not W["batched"] else 1,
         "clocks": clk,
         "impl": "ours",
     }
@@ -553,6 +561,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=1024)
     ap.add_argument("--ref-rows", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=("fused", "split"), default="fused",
+                    help="kernel structure: fused (one kernel per RK stage) or split (the paper's per-stage kernels)")
     ap.add_argument("--tune", action="store_true", help="also run the autotuner and time its launch")
     ap.add_argument("--tune-samples", type=int, default=1000)
     args = ap.parse_args()

@@ -109,19 +109,47 @@ typedef struct fv_kernel_cfg {
   int march;
 } fv_kernel_cfg;
 
-/* stage[s]: RK stage s+1 (fv_residual uses stage[0]); dt: time-step reduction. */
+/* Kernel structure of a stage.
+ * FV_FUSED (the default): one kernel per RK stage -- reconstruction, flux,
+ *   residual and update together (launch fields stage[] and dt).
+ * FV_SPLIT: the kernel structure of the paper's solver (Sec. 3.4): per axis a
+ *   limiter kernel (the MUSCL face states of Eq. (6)) and a flux kernel (the
+ *   Roe flux of every face), then a source kernel (-|Omega| S of Eq. (5), or
+ *   0), a right-hand-side kernel (the flux differences of Eq. (5)) and an
+ *   update kernel (the SSP-RK3 stage), with face states, fluxes and the
+ *   residual held in device memory between them: 7 kernels per stage in 2D,
+ *   9 in 3D.  Each is a grid-stride loop over its items (faces or cells, x
+ *   fastest) launched with split[k].grid CTAs (the paper's gang count; 0 =
+ *   one item per thread over the whole domain) of split[k].threads threads
+ *   (its vector length; 32..512, a multiple of 32); the other fields of
+ *   split[k] are ignored.  Slots: FV_SK_LIMITER + axis, FV_SK_FLUX + axis,
+ *   FV_SK_SOURCE, FV_SK_RHS, FV_SK_UPDATE (the z slots are unused in 2D).
+ *   The time-step reduction (dt) is the same as in FV_FUSED.  Batched
+ *   contexts support FV_FUSED only; the face-state, flux and residual arrays
+ *   (3 x nvar x faces per axis + nvar x cells doubles) are allocated on the
+ *   first split launch and kept by the context. */
+enum { FV_FUSED = 0, FV_SPLIT = 1 };
+enum { FV_SK_LIMITER = 0, FV_SK_FLUX = 3, FV_SK_SOURCE = 6, FV_SK_RHS = 7, FV_SK_UPDATE = 8, FV_SK_COUNT = 9 };
+
+/* stage[s]: RK stage s+1 (fv_residual uses stage[0]); dt: time-step
+ * reduction; mode: FV_FUSED or FV_SPLIT; split[]: the FV_SPLIT kernels
+ * (ignored, and may be zero, in FV_FUSED mode). */
 typedef struct fv_launch {
   fv_kernel_cfg stage[3];
   fv_kernel_cfg dt;
+  int mode;
+  fv_kernel_cfg split[FV_SK_COUNT];
 } fv_launch;
 
 typedef struct fv_ctx fv_ctx;
 
 /* Fill *l with the default launch configuration for grid g (one tile shape
- * and thread count for all stages): 2D 32x32 box tiles with 160 threads (256
- * in a batched context created without a launch); 3D
+ * and thread count for all stages): mode FV_FUSED; 2D 32x32 box tiles with
+ * 160 threads (256 in a batched context created without a launch); 3D
  * 8x8x8 box tiles with 192 threads; time-step reduction 512 threads, four
- * CTAs per SM.  Returns FV_EINVAL for a bad grid. */
+ * CTAs per SM; split kernels 128 threads, grid 0 (one item per thread: the
+ * analogue of a directive compiler's default vector length and gang count).
+ * Returns FV_EINVAL for a bad grid. */
 int fv_default_launch(const fv_grid *g, fv_launch *l);
 
 /* Create a solver context for ngrids grids.  ngrids = 1: one grid, 2D or 3D.
@@ -272,7 +300,7 @@ typedef struct fv_tune_report {
   double t_exhaustive;    /* s per step, best of the reduced space (0 if not run) */
   double r2_train, r2_test; /* Eq. (7) on run times, training / held-out samples */
   double space_size;      /* points in the full tuning space */
-  int n_params;           /* tuning parameters (14 in 2D, 20 in 3D) */
+  int n_params;           /* tuning parameters (fused: 14 in 2D, 20 in 3D; split: 14, 18) */
   int n_train, n_test, epochs, n_measured, n_exhaustive;
   int rounds, n_refined;  /* surrogate rounds run; measurements made by the refinement */
   int chosen;             /* the returned launch: 0 the search's, 1 the default, 2 the exhaustive best */
@@ -280,33 +308,41 @@ typedef struct fv_tune_report {
 } fv_tune_report;
 
 /* Tune the launch configuration of ctx for the state U (device or host; not
- * modified: timing runs on a copy in the context's staging buffer).  The space:
- * per RK-stage kernel tile_x in {8,16,32,64,128}, tile_y in {2,4,8,16,32}
- * (3D: tile_x {8,16,32}, tile_y {4,8,16}, tile_z {2,4,8}, and the kernel:
- * box tiles or z-marching with chunks of 8 x tile_z planes), threads in
- * {64,96,...,256}, loader in {TMA, plain}; time-step kernel threads in
- * {128,256,512,1024} and grid in {1,2,4,8} x SMs.  Procedure: time the
- * default launch and opts->samples random valid configurations; train the
- * network (features standardised, target log time standardised); score
- * opts->candidates random configurations; re-measure the opts->top best
- * predicted; repeat for opts->rounds rounds, each retrained on everything
- * measured so far (the held-out 25% of the random sample excepted); then
- * refine the best measured configuration by coordinate descent (each
- * parameter in turn over its value set).  Features are log2 of the
- * power-of-two parameters.  With opts->exhaustive, every configuration with
- * one shared (tile, threads) for the three stages, box tiles, TMA loads and
- * the default time-step kernel is timed as the judge.  Finally the search's
- * best, the default and (if run) the exhaustive best are timed interleaved
+ * modified: timing runs on a copy in the context's staging buffer), in the
+ * kernel structure of its current launch (mode).
+ * FV_SPLIT space, the paper's (Sec. 3.4, Table "tuning-parameters"): per
+ * split kernel a gang count (grid) in {100, 200, ..., 1000} and a vector
+ * length (threads) in {32, 64, ..., 384} -- 14 parameters over 10^7 x 12^7
+ * points in 2D, 18 in 3D.
+ * FV_FUSED space: per RK-stage kernel tile_x in {8,16,32,64,128}, tile_y in
+ * {2,4,8,16,32} (3D: tile_x {8,16,32}, tile_y {4,8,16}, tile_z {2,4,8}, and
+ * the kernel: box tiles or z-marching with chunks of 8 x tile_z planes),
+ * threads in {64,96,...,256}, loader in {TMA, plain}; time-step kernel
+ * threads in {128,256,512,1024} and grid in {1,2,4,8} x SMs.
+ * Procedure: time the default launch (a training sample when it lies in the
+ * space) and opts->samples random valid configurations; train the network
+ * (features: log2 of the parameters, standardised; target: log time,
+ * standardised); score opts->candidates random configurations; re-measure
+ * the opts->top best predicted; repeat for opts->rounds rounds, each
+ * retrained on everything measured so far (the held-out 25% of the random
+ * sample excepted); then refine the best measured configuration by
+ * coordinate descent (each parameter in turn over its value set).  With
+ * opts->exhaustive a judge is timed over a reduced space: FV_FUSED, every
+ * configuration with one shared (tile, threads) for the three stages, box
+ * tiles, TMA loads and the default time-step kernel; FV_SPLIT, one shared
+ * (gang, vector) for every kernel (120 points).  Finally the search's best,
+ * the default and (if run) the exhaustive best are timed interleaved
  * opts->final_repeats times; the fastest by median is returned in *best and
  * installed in ctx.  rep may be NULL.  Waits for completion. */
 int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *best, fv_tune_report *rep);
 
-/* The autotuner's search space for a dim-dimensional grid: *n_params tuning
- * parameters and *size points (the product of the value-set sizes listed at
- * fv_tune; the paper's analogue, Sec. 3.4, is 14 parameters over 10^7 x 12^7
- * points).  Host only: needs no GPU.  Returns FV_EINVAL unless dim is 2 or 3
- * and both pointers are non-NULL. */
-int fv_tune_space(int dim, int *n_params, double *size);
+/* The autotuner's search space for a dim-dimensional grid in kernel
+ * structure mode (FV_FUSED or FV_SPLIT): *n_params tuning parameters and
+ * *size points (the product of the value-set sizes listed at fv_tune; in 2D
+ * FV_SPLIT is the paper's space, Sec. 3.4: 14 parameters over 10^7 x 12^7
+ * points).  Host only: needs no GPU.  Returns FV_EINVAL unless dim is 2 or 3,
+ * mode is valid and both pointers are non-NULL. */
+int fv_tune_space(int dim, int mode, int *n_params, double *size);
 
 /* Residual R_h of Eq. (5) and, if rnorm2 != NULL, sum over cells of R_v^2 per
  * variable -- the same values as fv_residual -- without a context and without

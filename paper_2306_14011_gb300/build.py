@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfv.so")
 SOURCES = ["fv_api.cu", "fv_reduce.cu", "fv_stage2d.cu", "fv_stage3d.cu", "fv_noalloc.cu", "fv_mlp.cu",
-           "fv_tune.cu", "fv_batch.cu", "fv_adjoint.cu", "fv_march.cu"]
+           "fv_tune.cu", "fv_batch.cu", "fv_adjoint.cu", "fv_march.cu", "fv_split.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 # Resident 256-thread CTAs per SM the stage kernels' register budget targets

@@ -90,6 +90,7 @@ struct fv_ctx {
   double *norm_part;          // scratch: per-CTA partials (lazy)
   long long norm_part_cap;
   double *X1, *X2;            // adjoint work states (lazy)
+  double *split_buf;          // FV_SPLIT face states, fluxes and residual (lazy)
   std::vector<GraphEntry> graphs;
   const double *source;        // caller's cell-averaged source of Eq. (5), or null
   // host-pointer runs: copy-back stream and per-band events (lazy)
@@ -140,6 +141,12 @@ int validate_scheme(const fv_scheme *s) {
 }
 
 int validate_launch(const fv_grid *g, const fv_scheme *sch, const fv_launch *l, size_t smem_optin) {
+  if (l->mode != FV_FUSED && l->mode != FV_SPLIT) return FV_EINVAL;
+  if (l->mode == FV_SPLIT)
+    for (int k = 0; k < FV_SK_COUNT; ++k) {
+      const fv_kernel_cfg &q = l->split[k];
+      if (q.threads < 32 || q.threads > kSplitMaxThreads || q.threads % 32 || q.grid < 0) return FV_EINVAL;
+    }
   for (int s = 0; s < 3; ++s) {
     const fv_kernel_cfg &k = l->stage[s];
     if (k.march != 0 && (k.march != 1 || g->dim != 3)) return FV_EINVAL;
@@ -198,9 +205,99 @@ bool make_tmap(const fv_ctx *c, const double *U, const int tile[3], int march, C
   return r == CUDA_SUCCESS;
 }
 
+// Faces per axis of the split kernels: (n_d + 1) x the other extents.
+long long split_faces(const fv_grid &g, int d) {
+  long long f = 1;
+  for (int a = 0; a < 3; ++a) f *= (long long)g.n[a] + (a == d && d < g.dim ? 1 : 0);
+  return f;
+}
+
+int ensure_split(fv_ctx *c) {
+  if (c->split_buf) return FV_OK;
+  size_t doubles = (size_t)c->nv * (size_t)c->ncells;  // residual
+  for (int d = 0; d < c->grid.dim; ++d) doubles += 3 * (size_t)c->nv * (size_t)split_faces(c->grid, d);
+  FV_CK(cudaMalloc(&c->split_buf, sizeof(double) * doubles));
+  return FV_OK;
+}
+
+// CTAs of the split RHS kernel (= its norm partials) for the current launch.
+long long split_rhs_blocks(const fv_ctx *c) {
+  const fv_kernel_cfg &k = c->launch.split[FV_SK_RHS];
+  long long b = k.grid > 0 ? k.grid : (c->ncells + k.threads - 1) / k.threads;
+  return std::min<long long>(std::max<long long>(b, 1), 0x7fffffffLL);
+}
+
+// One residual evaluation or RK stage with the split kernels (FV_SPLIT).
+int split_stage(fv_ctx *c, int mode, const double *Us, const double *Un, double *out,
+                const unsigned long long *smax, double dt_fixed, double *norm_part, double *t_acc, cudaStream_t st) {
+  int r;
+  if ((r = ensure_split(c))) return r;
+  const fv_grid &g = c->grid;
+  SplitArgs a;
+  memset(&a, 0, sizeof(a));
+  a.dim = g.dim;
+  a.ncells = c->ncells;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = g.n[d];
+    a.bc[d][0] = g.bc[d][0];
+    a.bc[d][1] = g.bc[d][1];
+  }
+  double *p = c->split_buf;
+  a.R = mode == MODE_RESIDUAL ? out : p;
+  p += (size_t)c->nv * c->ncells;
+  for (int d = 0; d < g.dim; ++d) {
+    a.nface[d] = split_faces(g, d);
+    const size_t fsz = (size_t)c->nv * a.nface[d];
+    a.QL[d] = p;
+    a.QR[d] = p + fsz;
+    a.F[d] = p + 2 * fsz;
+    p += 3 * fsz;
+  }
+  a.Us = Us;
+  a.Un = Un;
+  a.out = out;
+  a.norm_part = norm_part;
+  a.S = c->source;
+  double h[3];
+  a.vol = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    h[d] = (d < g.dim) ? g.len[d] / g.n[d] : 1.0;
+    a.vol *= h[d];
+  }
+  a.inv_vol = 1.0 / a.vol;
+  for (int d = 0; d < 3; ++d) {
+    double ds = 1.0;
+    for (int e = 0; e < g.dim; ++e)
+      if (e != d) ds *= h[e];
+    a.half_ds[d] = 0.5 * ds;
+  }
+  a.limiter = c->scheme.limiter;
+  a.recon = c->scheme.recon;
+  a.inv_g1 = 1.0 / (c->scheme.gamma - 1.0);
+  a.cL = 0.25 * c->scheme.eps * (1.0 - c->scheme.kappa);
+  a.cR = 0.25 * c->scheme.eps * (1.0 + c->scheme.kappa);
+  a.g1 = c->scheme.gamma - 1.0;
+  a.half_eps = 0.5 * c->scheme.eps;
+  a.efix = c->scheme.efix;
+  a.inv2efix = c->scheme.efix > 0.0 ? 0.5 / c->scheme.efix : 0.0;
+  a.smax = smax;
+  a.cfl = c->scheme.cfl;
+  a.dt_fixed = dt_fixed;
+  a.t_acc = t_acc;
+  int grid[FV_SK_COUNT], threads[FV_SK_COUNT], rb = 0;
+  for (int k = 0; k < FV_SK_COUNT; ++k) {
+    grid[k] = c->launch.split[k].grid;
+    threads[k] = c->launch.split[k].threads;
+  }
+  FV_CK(launch_split(mode, a, grid, threads, &rb, st));
+  return FV_OK;
+}
+
 int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, double *out,
           const unsigned long long *smax, double dt_fixed, double *norm_part, double *t_acc, cudaStream_t st,
           long long tile_begin = 0, long long tile_count = 0) {
+  if (c->launch.mode == FV_SPLIT)  // whole-grid launches only (no tile ranges)
+    return split_stage(c, mode, Us, Un, out, smax, dt_fixed, norm_part, t_acc, st);
   const fv_grid &g = c->grid;
   const fv_kernel_cfg &k = c->launch.stage[sidx];
   StageArgs a;
@@ -528,7 +625,11 @@ int ctx_sm_count(const fv_ctx *c) { return c->sms; }
 int ctx_validate_launch(const fv_ctx *c, const fv_launch *l) {
   return validate_launch(&c->grid, &c->scheme, l, c->smem_optin);
 }
-int ctx_default_launch(const fv_ctx *c, fv_launch *l) { return fv_default_launch(&c->grid, l); }
+int ctx_default_launch(const fv_ctx *c, fv_launch *l) {
+  const int r = fv_default_launch(&c->grid, l);
+  l->mode = c->launch.mode;  // the default of the context's kernel structure
+  return r;
+}
 int ctx_dim(const fv_ctx *c) { return c->grid.dim; }
 
 }  // namespace fvk
@@ -569,6 +670,11 @@ int fv_default_launch(const fv_grid *g, fv_launch *l) {
   }
   l->dt.threads = 512;  // 1024 threads per SM keep enough loads in flight
   l->dt.grid = 0;
+  l->mode = FV_FUSED;
+  for (int k = 0; k < FV_SK_COUNT; ++k) {
+    l->split[k].threads = 128;
+    l->split[k].grid = 0;
+  }
   return FV_OK;
 }
 
@@ -609,6 +715,7 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
       for (int s = 0; s < 3; ++s) c->launch.stage[s].threads = 256;
   }
   if ((r = validate_launch(&c->grid, &c->scheme, &c->launch, c->smem_optin))) return fail(r);
+  if (ngrids > 1 && c->launch.mode != FV_FUSED) return fail(FV_EUNSUPPORTED);
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(FV_ECUDA);
   if (cudaMalloc(&c->U1, c->state_bytes) != cudaSuccess || cudaMalloc(&c->U2, c->state_bytes) != cudaSuccess)
     return fail(cuda_fail(cudaErrorMemoryAllocation));
@@ -626,6 +733,7 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
     return fail(cuda_fail(cudaErrorMemoryAllocation));
   if ((r = set_attributes(c))) return fail(r);
   if (c->ngrids > 1 && (r = batch_setup(c))) return fail(r);
+  if (c->launch.mode == FV_SPLIT && (r = ensure_split(c))) return fail(r);  // never inside a graph capture
   *out = c;
   return FV_OK;
 }
@@ -645,6 +753,8 @@ int fv_set_launch(fv_ctx *c, const fv_launch *l) {
   if (!c || !l) return FV_EINVAL;
   int r = validate_launch(&c->grid, &c->scheme, l, c->smem_optin);
   if (r) return r;
+  if (c->ngrids > 1 && l->mode != FV_FUSED) return FV_EUNSUPPORTED;
+  if (l->mode == FV_SPLIT && (r = ensure_split(c))) return r;
   c->launch = *l;
   drop_graphs(c);
   if ((r = set_attributes(c))) return r;
@@ -687,7 +797,7 @@ int fv_residual(fv_ctx *c, const double *U, double *R, double *rnorm2) {
   double *part = nullptr;
   int nt[3];
   ntiles(c->grid, c->launch.stage[0].tile, nt);
-  const long long nblk = (long long)nt[0] * nt[1] * nt[2];
+  const long long nblk = c->launch.mode == FV_SPLIT ? split_rhs_blocks(c) : (long long)nt[0] * nt[1] * nt[2];
   if (rnorm2) {
     if (c->norm_part_cap < nblk) {
       if (c->norm_part) cudaFree(c->norm_part);
@@ -870,14 +980,15 @@ int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
     (pass == 0 ? gK : g1) = exec;
   }
   // on a host state the last step runs outside the graphs, overlapping its
-  // copy back with the last stage kernel
-  for (int left = hostU ? nsteps - 1 : nsteps; left > 0;) {
+  // copy back with the last stage kernel (fused kernels: they run by tile rows)
+  const bool banded = hostU && c->launch.mode == FV_FUSED;
+  for (int left = banded ? nsteps - 1 : nsteps; left > 0;) {
     const int steps = left >= K ? K : 1;
     FV_CK(cudaGraphLaunch(steps == K ? gK : g1, c->stream));
     left -= steps;
   }
   if (hostU) {
-    if (nsteps > 0) {
+    if (banded && nsteps > 0) {
       if ((r = last_step_to_host(c, Ud, U, dt_fixed, cfl))) return r;
     } else {
       FV_CK(cudaMemcpyAsync(U, Ud, c->state_bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -980,6 +1091,7 @@ void fv_destroy(fv_ctx *c) {
   if (c->norm_part) cudaFree(c->norm_part);
   if (c->X1) cudaFree(c->X1);
   if (c->X2) cudaFree(c->X2);
+  if (c->split_buf) cudaFree(c->split_buf);
   if (c->b_prob) cudaFree(c->b_prob);
   if (c->b_tile_begin) cudaFree(c->b_tile_begin);
   if (c->b_chunk_begin) cudaFree(c->b_chunk_begin);

@@ -7,6 +7,8 @@ namespace fvk {
 
 // Largest CTA of the 3D box-tiled stage kernel (its register budget).
 constexpr int kStage3dMaxThreads = 192;
+// Largest CTA of the split kernels (FV_SPLIT; their register budget).
+constexpr int kSplitMaxThreads = 512;
 
 // Work of one launch of the fused stage kernel.
 enum StageMode : int {
@@ -93,6 +95,41 @@ struct BatchArgs {
   double g1, gamma, half_eps, efix, inv2efix, cfl, dt_fixed;
   float g1f, gammaf;
 };
+
+// The split kernel structure (fv_launch.mode = FV_SPLIT): per axis a limiter
+// kernel writing the MUSCL face states QL, QR and a flux kernel writing 2F
+// (the Roe routine's output), then source, right-hand-side and update
+// kernels.  Face arrays of axis d are [nvar][nface[d]] with faces indexed x
+// fastest over (n[0] + (d == 0)) x (n[1] + (d == 1)) x (n[2] + (d == 2)); face
+// m along d lies between cells m - 1 and m.
+struct SplitArgs {
+  int dim;
+  int n[3];
+  int bc[3][2];
+  long long ncells;
+  long long nface[3];
+  const double *Us;          // state whose residual is evaluated
+  const double *Un;          // U^n for stages 2 and 3
+  double *out;               // the next stage state (stage modes)
+  double *QL[3], *QR[3];     // face states per axis
+  double *F[3];              // 2F per axis
+  double *R;                 // the residual (the output in residual mode)
+  double *norm_part;         // residual mode: per-CTA partial sums of R_v^2 of the RHS kernel, or null
+  const double *S;           // source of Eq. (5), or null
+  double vol, inv_vol;       // |Omega| and 1 / |Omega|
+  int limiter, recon;        // FV_LIM_*, FV_RECON_*
+  double inv_g1, cL, cR, g1, half_eps, efix, inv2efix;
+  double half_ds[3];         // face area / 2 per axis
+  const unsigned long long *smax;  // CFL mode: bits of the max wave-speed sum, else null
+  double cfl, dt_fixed;
+  double *t_acc;             // stage 3: simulated time (one thread adds dt), or null
+};
+// Launch the split kernels of one residual evaluation (mode MODE_RESIDUAL) or
+// RK stage: grid[k], threads[k] for slot k of FV_SK_* (grid 0: one item per
+// thread).  *rhs_blocks receives the RHS kernel's CTA count (the number of
+// norm partials).
+cudaError_t launch_split(int mode, const SplitArgs &a, const int *grid, const int *threads, int *rhs_blocks,
+                         cudaStream_t st);
 
 // Adjoint (vector-Jacobian product) kernel: out = sum_d scale_d J_d(U)^T lam
 // + cA A + cB B + cC C (A, B, C may be null).

@@ -5,10 +5,13 @@
 // parameters, Table "tuning-parameters") by timing a random sample of
 // configurations, fitting a fully connected ReLU network (Adam, Table
 // "para-setting") to run time on standardised features, and using the model
-// to find fast configurations.  Here the kernels are the three fused RK-stage
-// kernels and the time-step reduction; their parameters are tile shape,
-// threads per CTA and tile loader per stage, plus the reduction's threads and
-// grid: 14 parameters in 2D (17 in 3D).  Random numbers come from SplitMix64
+// to find fast configurations.  Two spaces, after the context's kernel
+// structure: FV_SPLIT is the paper's own -- gang count (CTAs) and vector
+// length (threads) of each split kernel over the Table's value sets, 14
+// parameters in 2D, 18 in 3D; FV_FUSED tunes the three fused RK-stage kernels
+// and the time-step reduction -- tile shape, threads per CTA and tile loader
+// per stage (and the 3D kernel kind), plus the reduction's threads and grid:
+// 14 parameters in 2D, 20 in 3D.  Random numbers come from SplitMix64
 // (Steele, Lea and Flood, 2014).
 #include <algorithm>
 #include <cmath>
@@ -40,13 +43,31 @@ struct SplitMix64 {
 };
 
 struct Space {
-  int dim, per_stage, nparams;
+  int dim, mode, per_stage, nparams;
   std::vector<std::vector<int>> vals;
+  std::vector<int> slots;  // FV_SPLIT: the split kernel of each (gang, vector) pair
 };
 
-Space make_space(int dim) {
+Space make_space(int dim, int mode) {
   Space sp;
   sp.dim = dim;
+  sp.mode = mode;
+  sp.per_stage = 0;
+  if (mode == FV_SPLIT) {
+    // Table "tuning-parameters": gang 100..1000 step 100, vector 32..384 step 32
+    std::vector<int> gang, vector;
+    for (int g = 100; g <= 1000; g += 100) gang.push_back(g);
+    for (int v = 32; v <= 384; v += 32) vector.push_back(v);
+    for (int d = 0; d < dim; ++d) sp.slots.push_back(FV_SK_LIMITER + d);
+    for (int d = 0; d < dim; ++d) sp.slots.push_back(FV_SK_FLUX + d);
+    sp.slots.insert(sp.slots.end(), {FV_SK_SOURCE, FV_SK_RHS, FV_SK_UPDATE});
+    for (size_t q = 0; q < sp.slots.size(); ++q) {
+      sp.vals.push_back(gang);
+      sp.vals.push_back(vector);
+    }
+    sp.nparams = (int)sp.vals.size();
+    return sp;
+  }
   const std::vector<int> threads = {64, 96, 128, 160, 192, 224, 256};
   for (int s = 0; s < 3; ++s) {
     if (dim == 2) {
@@ -70,9 +91,21 @@ Space make_space(int dim) {
 
 typedef std::vector<int> Cfg;  // index into each value set
 
-fv_launch to_launch(const Space &sp, const Cfg &c, int sms) {
+// The launch of configuration c; `base` supplies what the space leaves fixed
+// (FV_SPLIT: the fused stage and time-step fields).
+fv_launch to_launch(const Space &sp, const Cfg &c, int sms, const fv_launch &base) {
   fv_launch l;
-  memset(&l, 0, sizeof(l));
+  if (sp.mode == FV_SPLIT) {
+    l = base;
+    l.mode = FV_SPLIT;
+    for (size_t q = 0; q < sp.slots.size(); ++q) {
+      l.split[sp.slots[q]].grid = sp.vals[2 * q][c[2 * q]];
+      l.split[sp.slots[q]].threads = sp.vals[2 * q + 1][c[2 * q + 1]];
+    }
+    return l;
+  }
+  l = base;
+  l.mode = FV_FUSED;
   for (int s = 0; s < 3; ++s) {
     const int b = s * sp.per_stage;
     fv_kernel_cfg &k = l.stage[s];
@@ -92,8 +125,8 @@ fv_launch to_launch(const Space &sp, const Cfg &c, int sms) {
   return l;
 }
 
-// Features: log2 of the power-of-two parameters (tiles, thread counts, grid
-// multiplier), the loader and the 3D kernel choice as 0/1.
+// Features: log2 of the numeric parameters (tiles, thread counts, grid
+// multiplier, gang counts), the loader and the 3D kernel choice as 0/1.
 void features(const Space &sp, const Cfg &c, double *f) {
   for (int p = 0; p < sp.nparams; ++p) {
     const int v = sp.vals[p][c[p]];
@@ -118,6 +151,15 @@ bool cfg_of(const Space &sp, const fv_launch &l, int sms, Cfg *out) {
       }
     return false;
   };
+  if (sp.mode == FV_SPLIT) {
+    if (l.mode != FV_SPLIT) return false;
+    for (size_t q = 0; q < sp.slots.size(); ++q)
+      if (!find((int)(2 * q), l.split[sp.slots[q]].grid) || !find((int)(2 * q + 1), l.split[sp.slots[q]].threads))
+        return false;
+    *out = c;
+    return true;
+  }
+  if (l.mode != FV_FUSED) return false;
   for (int s = 0; s < 3; ++s) {
     const int b = s * sp.per_stage;
     const fv_kernel_cfg &k = l.stage[s];
@@ -167,9 +209,9 @@ struct DevBuf {
 
 }  // namespace
 
-extern "C" int fv_tune_space(int dim, int *n_params, double *size) {
-  if ((dim != 2 && dim != 3) || !n_params || !size) return FV_EINVAL;
-  const Space sp = make_space(dim);
+extern "C" int fv_tune_space(int dim, int mode, int *n_params, double *size) {
+  if ((dim != 2 && dim != 3) || (mode != FV_FUSED && mode != FV_SPLIT) || !n_params || !size) return FV_EINVAL;
+  const Space sp = make_space(dim, mode);
   double points = 1.0;
   for (auto &v : sp.vals) points *= (double)v.size();
   *n_params = sp.nparams;
@@ -205,7 +247,10 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
   if (h.max_epochs <= 0) h.max_epochs = 200;
   if (h.n_iter_no_change <= 0) h.n_iter_no_change = 10;
   const int dim = ctx_dim(ctx), sms = ctx_sm_count(ctx);
-  const Space sp = make_space(dim);
+  fv_launch deflt;  // the library default: the analogue of the compiler's default launch
+  int r;
+  if ((r = ctx_default_launch(ctx, &deflt))) return r;
+  const Space sp = make_space(dim, deflt.mode);
   const int nf = sp.nparams;
   std::vector<int> sizes;
   sizes.push_back(nf);
@@ -214,7 +259,6 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
   sizes.push_back(1);
   const int nl = (int)sizes.size() - 1;
 
-  int r;
   double *Uw = nullptr;
   if ((r = ctx_work_state(ctx, U, &Uw))) return r;
   SplitMix64 rng{o.seed};
@@ -228,7 +272,7 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
   auto measure = [&](const Cfg &c, bool holdout, int *outcome) -> int {
     *outcome = 0;
     if (!seen.insert(key(sp, c)).second) return FV_OK;
-    const fv_launch l = to_launch(sp, c, sms);
+    const fv_launch l = to_launch(sp, c, sms, deflt);
     double t = 0.0;
     const int rr = ctx_time_launch(ctx, Uw, &l, o.steps, o.repeats, &t);
     if (rr == FV_EINVAL) return FV_OK;  // outside the device limits (shared memory)
@@ -248,8 +292,6 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
   // ---- 1. time the default launch (a training sample) and a random sample of
   // valid configurations (25% held out)
   int outcome;
-  fv_launch deflt;  // the library default: the analogue of the compiler's default launch
-  if ((r = ctx_default_launch(ctx, &deflt))) return r;
   {
     Cfg c0;
     if (cfg_of(sp, deflt, sms, &c0) && (r = measure(c0, false, &outcome))) return r;
@@ -280,7 +322,7 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
     for (int attempts = 0; (int)cand.size() < o.candidates && attempts < 4 * o.candidates; ++attempts) {
       Cfg c = random_cfg(sp, rng);
       if (!cseen.insert(key(sp, c)).second) continue;
-      const fv_launch l = to_launch(sp, c, sms);
+      const fv_launch l = to_launch(sp, c, sms, deflt);
       if (ctx_validate_launch(ctx, &l) != FV_OK) continue;  // cannot launch (shared memory)
       cand.push_back(c);
     }
@@ -402,13 +444,32 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
     }
     if (!improved) break;
   }
-  fv_launch tuned = to_launch(sp, cfgs[best_i], sms);
+  fv_launch tuned = to_launch(sp, cfgs[best_i], sms, deflt);
 
   // ---- 4. exhaustive judge on the reduced space (shared tile and threads)
   fv_launch exh_best;
   memset(&exh_best, 0, sizeof(exh_best));
   int n_exh = 0;
-  if (o.exhaustive) {
+  if (o.exhaustive && sp.mode == FV_SPLIT) {  // one shared (gang, vector) for every split kernel
+    double t_exh = INFINITY;
+    for (int gang : sp.vals[0])
+      for (int vec : sp.vals[1]) {
+        fv_launch l = deflt;
+        for (int slot : sp.slots) {
+          l.split[slot].grid = gang;
+          l.split[slot].threads = vec;
+        }
+        double t = 0.0;
+        r = ctx_time_launch(ctx, Uw, &l, o.steps, o.repeats, &t);
+        if (r == FV_EINVAL) continue;
+        if (r) return r;
+        ++n_exh;
+        if (t < t_exh) {
+          t_exh = t;
+          exh_best = l;
+        }
+      }
+  } else if (o.exhaustive) {
     std::vector<std::vector<int>> axes;
     if (dim == 2)
       axes = {sp.vals[0], sp.vals[1], {1}, sp.vals[2]};

@@ -50,8 +50,13 @@ class fv_kernel_cfg(C.Structure):
                 ("march", C.c_int)]
 
 
+FV_FUSED, FV_SPLIT = 0, 1
+FV_SK_LIMITER, FV_SK_FLUX, FV_SK_SOURCE, FV_SK_RHS, FV_SK_UPDATE, FV_SK_COUNT = 0, 3, 6, 7, 8, 9
+
+
 class fv_launch(C.Structure):
-    _fields_ = [("stage", fv_kernel_cfg * 3), ("dt", fv_kernel_cfg)]
+    _fields_ = [("stage", fv_kernel_cfg * 3), ("dt", fv_kernel_cfg), ("mode", C.c_int),
+                ("split", fv_kernel_cfg * FV_SK_COUNT)]
 
 
 class fv_mlp_hyper(C.Structure):
@@ -109,7 +114,7 @@ def load() -> C.CDLL:
         L.fv_mlp_predict.restype = C.c_int
         L.fv_tune.argtypes = [_VP, _VP, P(fv_tune_opts), P(fv_launch), P(fv_tune_report)]
         L.fv_tune.restype = C.c_int
-        L.fv_tune_space.argtypes = [C.c_int, P(C.c_int), P(C.c_double)]
+        L.fv_tune_space.argtypes = [C.c_int, C.c_int, P(C.c_int), P(C.c_double)]
         L.fv_tune_space.restype = C.c_int
         L.fv_set_source.argtypes = [_VP, _VP]
         L.fv_set_source.restype = C.c_int
@@ -161,11 +166,19 @@ def make_scheme(gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, limiter=FV_LI
 def launch_to_dict(l: fv_launch) -> dict:
     st = [dict(tile=tuple(l.stage[s].tile), threads=l.stage[s].threads, loader=l.stage[s].loader,
                march=l.stage[s].march) for s in range(3)]
-    return dict(stage=st, dt=dict(threads=l.dt.threads, grid=l.dt.grid))
+    sp = [dict(grid=l.split[k].grid, threads=l.split[k].threads) for k in range(FV_SK_COUNT)]
+    return dict(stage=st, dt=dict(threads=l.dt.threads, grid=l.dt.grid), mode=l.mode, split=sp)
 
 
 def launch_from_dict(d: dict) -> fv_launch:
+    """The inverse of launch_to_dict; "mode" defaults to FV_FUSED and "split"
+    (a list of FV_SK_COUNT dicts with grid and threads) may be omitted in
+    FV_FUSED mode."""
     l = fv_launch()
+    l.mode = d.get("mode", FV_FUSED)
+    for k, e in enumerate(d.get("split", [])):
+        l.split[k].grid = e.get("grid", 0)
+        l.split[k].threads = e["threads"]
     for s in range(3):
         e = d["stage"][s]
         for a in range(3):
@@ -338,11 +351,12 @@ def fv_tune(ctx: int, U, **opts):
     return launch_to_dict(best), report
 
 
-def fv_tune_space(dim: int):
-    """(number of tuning parameters, points in the search space) for a dim-D grid."""
+def fv_tune_space(dim: int, mode: int = FV_FUSED):
+    """(number of tuning parameters, points in the search space) for a dim-D
+    grid in kernel structure `mode`."""
     n = C.c_int(0)
     size = C.c_double(0.0)
-    _check(load().fv_tune_space(dim, C.byref(n), C.byref(size)), "fv_tune_space")
+    _check(load().fv_tune_space(dim, mode, C.byref(n), C.byref(size)), "fv_tune_space")
     return n.value, size.value
 
 
@@ -391,11 +405,14 @@ class Solver:
     Solver(grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1,
            launch=None (dict or fv_launch), stream=None (torch's current stream),
            limiter=FV_LIM_MINMOD | FV_LIM_VANLEER | FV_LIM_NONE,
-           recon=FV_RECON_CONSERVED | FV_RECON_PRIMITIVE)
+           recon=FV_RECON_CONSERVED | FV_RECON_PRIMITIVE,
+           mode=None | FV_FUSED | FV_SPLIT)
+    mode, when given, selects the kernel structure: with launch=None it starts
+    from the library's default launch; it overrides the mode of a given launch.
     """
 
     def __init__(self, grid, gamma=1.4, cfl=0.5, eps=1.0, kappa=-1.0, efix=0.1, launch=None, stream=None,
-                 limiter=FV_LIM_MINMOD, recon=FV_RECON_CONSERVED):
+                 limiter=FV_LIM_MINMOD, recon=FV_RECON_CONSERVED, mode=None):
         self.batched = isinstance(grid, (list, tuple))
         self.grids = list(grid) if self.batched else [grid]
         self.grid = self.grids[0]
@@ -403,6 +420,10 @@ class Solver:
         self.scheme = make_scheme(gamma, cfl, eps, kappa, efix, limiter, recon)
         if isinstance(launch, dict):
             launch = launch_from_dict(launch)
+        if mode is not None:
+            if launch is None:
+                launch = fv_default_launch(self.grid)
+            launch.mode = mode
         self.ctx = fv_init(grid, self.scheme, launch, stream)
         self.offsets = fv_layout(self.ctx, self.ngrids)
 

@@ -48,6 +48,12 @@ def test_strerror_and_default_launch_without_gpu():
     assert l2.dt.threads == 512 and l2.dt.grid == 0
     l3 = fv.fv_default_launch(I.grid3d(16, 16, 16, 1.0, 1.0, 1.0))
     assert tuple(l3.stage[2].tile) == (8, 8, 8) and l3.stage[2].threads == 192 and l3.stage[2].march == 0
+    # fused by default; the split kernels default to 128 threads, one item per thread
+    for l in (l2, l3):
+        assert l.mode == fv.FV_FUSED
+        assert all(l.split[k].threads == 128 and l.split[k].grid == 0 for k in range(fv.FV_SK_COUNT))
+    d = fv.launch_to_dict(l2)
+    assert fv.launch_to_dict(fv.launch_from_dict(d)) == d
 
 
 def test_invalid_grids_are_rejected_on_the_host():
@@ -85,17 +91,18 @@ def test_init_without_a_gpu_reports_an_error_not_a_crash():
 
 
 def test_tuning_space_sizes():
-    """The tuner's space, and the paper's Table space (Sec. 3.4: 7 kernels with
-    gang 100, 200, ..., 1000 and vector length 32, 64, ..., 384 each) counted
-    the same way: the paper states 10^7 x 12^7 = 3.58e14 points."""
+    """The split kernels' space is the paper's (Sec. 3.4, Table
+    "tuning-parameters": 7 kernels, each with 10 gang and 12 vector-length
+    values; the paper states 14 parameters and 3.58e14 points); 3D adds a
+    limiter and a flux kernel.  The fused space counts its own value sets."""
+    n, size = fv.fv_tune_space(2, fv.FV_SPLIT)
+    assert n == 14 and size == float(10 ** 7 * 12 ** 7) and f"{size:.2e}" == "3.58e+14"
+    assert fv.fv_tune_space(3, fv.FV_SPLIT) == (18, float(10 ** 9 * 12 ** 9))
     assert fv.fv_tune_space(2) == (14, float((5 * 5 * 7 * 2) ** 3 * 4 * 4))
-    assert fv.fv_tune_space(3) == (20, float((3 * 3 * 3 * 7 * 2 * 2) ** 3 * 4 * 4))
-    gang, vector = range(100, 1001, 100), range(32, 385, 32)
-    assert (len(gang), len(vector)) == (10, 12)
-    paper_points = len(gang) ** 7 * len(vector) ** 7
-    assert paper_points == 10 ** 7 * 12 ** 7 and f"{paper_points:.2e}" == "3.58e+14"
-    with pytest.raises(fv.FvError):
-        fv.fv_tune_space(4)
+    assert fv.fv_tune_space(3, fv.FV_FUSED) == (20, float((3 * 3 * 3 * 7 * 2 * 2) ** 3 * 4 * 4))
+    for dim, mode in [(4, fv.FV_FUSED), (2, 2), (3, -1)]:
+        with pytest.raises(fv.FvError):
+            fv.fv_tune_space(dim, mode)
 
 
 def test_debug_wait_rejects_bad_arguments_on_the_host():
