@@ -73,6 +73,13 @@ int orc_residual(const Grid *g, const Scheme *s, const double *U, double *R, con
 // The residual evaluated in extended precision (long double: 64-bit or
 // 113-bit significand depending on the host) from the same double inputs,
 // for measuring the rounding error of FP64 evaluations.
+// Per cell and variable, sum_d ds_d (|F_{k+1/2,d}| + |F_{k-1/2,d}|) + |Omega| |S|:
+// the magnitude of the terms the residual of Eq. (5) adds up.
+int orc_residual_terms(const Grid *g, const Scheme *s, const double *U, double *R, const double *S) {
+  residual<double, true>(*g, *s, U, R, S);
+  return 0;
+}
+
 int orc_residual_ext(const Grid *g, const Scheme *s, const double *U, double *R, const double *S) {
   Layout L(*g);
   size_t N = L.cells() * L.nv;

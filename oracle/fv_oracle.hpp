@@ -301,7 +301,10 @@ void pad(const Grid &g, const Layout &L, const T *U, std::vector<T> &P) {
 // dy*dz in 3D), F_{k+1/2,d} the Roe flux between the MUSCL states of Eq. (6)
 // (inviscid: no viscous flux) and S the cell-averaged source (S = NULL: 0).
 // Each face flux is evaluated once, stored, and read by both cells that share it.
-template <class T>
+// TERMS = true instead accumulates the magnitudes of the terms that sum:
+// sum_d ds_d (|F_{k+1/2,d}| + |F_{k-1/2,d}|) + |Omega| |S_k| (the scale of
+// the residual's rounding error, used to judge residuals that vanish).
+template <class T, bool TERMS = false>
 void residual(const Grid &g, const Scheme &s, const T *U, T *R, const double *S = nullptr) {
   Layout L(g);
   std::vector<T> P;
@@ -352,14 +355,24 @@ void residual(const Grid &g, const Scheme &s, const T *U, T *R, const double *S 
       int i = (int)(cidx % L.n[0]), j = (int)((cidx / L.n[0]) % L.n[1]), k = (int)(cidx / ((long)L.n[0] * L.n[1]));
       long lo = ((long)k * fn[1] + j) * fn[0] + i;                             // face k-1/2
       long hi = ((long)(k + e[2]) * fn[1] + (j + e[1])) * fn[0] + (i + e[0]);  // face k+1/2
-      for (int v = 0; v < nv; ++v)
-        R[(size_t)v * ncell + cidx] += (F[(size_t)v * nface + hi] - F[(size_t)v * nface + lo]) * ds;
+      for (int v = 0; v < nv; ++v) {
+        const T Fh = F[(size_t)v * nface + hi], Fl = F[(size_t)v * nface + lo];
+        if constexpr (TERMS)
+          R[(size_t)v * ncell + cidx] += (std::fabs(Fh) + std::fabs(Fl)) * ds;
+        else
+          R[(size_t)v * ncell + cidx] += (Fh - Fl) * ds;
+      }
     }
   }
   if (S) {
     double vol = 1.0;
     for (int a = 0; a < L.dim; ++a) vol *= L.h[a];
-    for (long c = 0; c < ncell * nv; ++c) R[c] = R[c] - vol * T(S[c]);
+    for (long c = 0; c < ncell * nv; ++c) {
+      if constexpr (TERMS)
+        R[c] = R[c] + vol * std::fabs(T(S[c]));
+      else
+        R[c] = R[c] - vol * T(S[c]);
+    }
   }
 }
 

@@ -61,6 +61,7 @@ def load_library(path: str):
         L.orc_run.argtypes = [GP, SP, _D, C.c_int, C.c_double, C.c_double, _D]
         L.orc_run.restype = C.c_double
         L.orc_residual_ext.argtypes = [GP, SP, _D, _D, _D]
+        L.orc_residual_terms.argtypes = [GP, SP, _D, _D, _D]
         L.orc_residual_cells.argtypes = [GP, SP, _D, C.c_long, _L, _D]
         L.orc_residual_cells_ext.argtypes = [GP, SP, _D, C.c_long, _L, _D]
         L.orc_roe_flux.argtypes = [SP, C.c_int, C.c_int, _D, _D, _D]
@@ -115,6 +116,17 @@ def residual_ext(g, U, s: Scheme | None = None, S=None) -> np.ndarray:
     S = None if S is None else _check(g, S)
     lib().orc_residual_ext(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), _ptr(R),
                            None if S is None else _ptr(S))
+    return R
+
+
+def residual_terms(g, U, s: Scheme | None = None, S=None) -> np.ndarray:
+    """Per cell and variable, the sum of the magnitudes of the terms R_h adds
+    (face fluxes times face areas, and |Omega| |S|): the scale of its rounding."""
+    U = _check(g, U)
+    R = np.empty_like(U)
+    S = None if S is None else _check(g, S)
+    lib().orc_residual_terms(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), _ptr(R),
+                             None if S is None else _ptr(S))
     return R
 
 

@@ -201,14 +201,26 @@ __device__ __forceinline__ bool wave_sum32(const double *U, long long N, long lo
 }
 
 // ------------------------------------------------------------ Roe flux
+// 2 min(x, 0) on the integer pipe: 2x for x < 0 (an exponent increment, see
+// scale_pow2), +0 for x >= 0 and for -0.
+__device__ __forceinline__ double twice_min0(double x) {
+  const bool neg = __double2hiint(x) < 0 && !izero(x);
+  return isel(neg, scale_pow2<1>(x), 0.0);
+}
+
 // Twice the Roe flux across a face with unit normal along one axis.  States
 // are ordered normal-first: q = (rho, m_n, m_t[0..NT-1], rho*e_t), where m_n
 // is the momentum along the face normal and m_t the tangential momenta.
-//   2F = F(QL) + F(QR) - sum_w |lambda_w| alpha_w r_w
-// acoustic waves alpha_{1,3} = (dp -+ rho~ c~ du_n) / (2 c~^2), entropy wave
-// alpha_2 = drho - dp / c~^2, shear waves rho~ du_t, eigenvalues u~_n -+ c~
-// and u~_n; Harten's fix replaces |lambda| by (lambda^2 + delta^2)/(2 delta)
-// for the acoustic waves when |lambda| < delta = efix * c~.
+// The flux is  F = (F(QL) + F(QR))/2 - sum_w |lambda_w| alpha_w r_w / 2
+// with acoustic waves alpha_{1,3} = (dp -+ rho~ c~ du_n) / (2 c~^2), entropy
+// wave alpha_2 = drho - dp / c~^2, shear waves rho~ du_t, eigenvalues
+// u~_n -+ c~ and u~_n; Harten's fix replaces |lambda| by (lambda^2 +
+// delta^2)/(2 delta) for the acoustic waves when |lambda| < delta = efix c~.
+// Roe's averages make F(QR) - F(QL) = sum_w lambda_w alpha_w r_w exactly (in
+// exact arithmetic), so the same flux is evaluated one-sided, without F(QR):
+//   2F = 2 F(QL) + sum_w mu_w alpha_w r_w,   mu_w = lambda_w - |lambda_w|
+// (mu_w = 2 min(lambda_w, 0) on the integer pipe unless the fix applies).
+// Free streams give 2F(Q) exactly; fully supersonic faces give 2F(QL) exactly.
 // g1 = gamma - 1; inv2efix = 1 / (2 efix) (unused when efix = 0).
 template <int NT>
 __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
@@ -266,37 +278,37 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   const double c = c2 * tc;
   const double ic2 = tc * tc;        // 1/c~^2
 
-  // wave strengths
+  // wave strengths alpha_{1,3} = dp / (2 c~^2) -+ rho~ du_n / (2 c~)
   const double drho = QR[0] - QL[0];
   const double dp = pR - pL;
-  const double rcdun = (rho * c) * dun;
-  const double hic2 = half_nonneg(ic2);
-  const double a1 = (dp - rcdun) * hic2;
-  const double a3 = (dp + rcdun) * hic2;
+  const double P2 = dp * half_nonneg(ic2);
+  const double Q2 = (rho * dun) * half_nonneg(tc);
+  const double a1 = P2 - Q2;
+  const double a3 = P2 + Q2;
   const double a2 = fma(-dp, ic2, drho);
 
-  // |eigenvalues| (sign handling on the integer pipe), entropy fix.  Whether
-  // |lambda| < delta = efix c~ is decided in FP32 (operands truncated on the
-  // integer pipe): the fixed |lambda| equals delta at |lambda| = delta, so a
-  // decision flipped within FP32 resolution changes the flux by
+  // mu_w = lambda_w - |lambda_w|, with the entropy fix.  Whether |lambda| <
+  // delta = efix c~ is decided in FP32 (operands truncated on the integer
+  // pipe): the fixed |lambda| equals delta at |lambda| = delta, so a decision
+  // flipped within FP32 resolution changes the flux by
   // O(((|lambda| - delta) / delta)^2 delta), below FP64 rounding.
-  double l1 = iabs(un - c);
-  double l3 = iabs(un + c);
-  const double l2 = iabs(un);
+  const double lam1 = un - c, lam3 = un + c;
+  double m1 = twice_min0(lam1), m3 = twice_min0(lam3);
+  const double m2 = twice_min0(un);
   const float deltaf = __fmul_rn(f32_trunc(efix), f32_trunc(c));
-  const bool fix1 = f32_trunc(l1) < deltaf, fix3 = f32_trunc(l3) < deltaf;
+  const bool fix1 = f32_trunc(iabs(lam1)) < deltaf, fix3 = f32_trunc(iabs(lam3)) < deltaf;
   // near sonic points only: a warp-uniform branch keeps the (rare) fix from
   // being computed unconditionally
   if (__any_sync(__activemask(), fix1 || fix3)) {
     const double delta = efix * c;
-    const double d2 = delta * delta, s2 = tc * inv2efix;
-    l1 = isel(fix1, fma(l1, l1, d2) * s2, l1);
-    l3 = isel(fix3, fma(l3, l3, d2) * s2, l3);
+    const double d2 = delta * delta, s2 = tc * inv2efix;  // s2 = 1 / (2 delta)
+    m1 = isel(fix1, fma(-fma(lam1, lam1, d2), s2, lam1), m1);
+    m3 = isel(fix3, fma(-fma(lam3, lam3, d2), s2, lam3), m3);
   }
 
-  // dissipation sum_w |lambda_w| alpha_w r_w
-  const double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3;
-  const double lr = l2 * rho;
+  // sum_w mu_w alpha_w r_w
+  const double A1 = m1 * a1, A2 = m2 * a2, A3 = m3 * a3;
+  const double lr = m2 * rho;
   const double s13 = A1 + A3;
   const double cd13 = c * (A3 - A1);
   const double D0 = s13 + A2;
@@ -311,12 +323,13 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   }
   DE = fma(H, s13, fma(un, cd13, DE));
 
-  // F(QL) + F(QR) - dissipation
-  G[0] = (QL[1] + QR[1]) - D0;
-  G[1] = (fma(QL[1], unL, pL) + fma(QR[1], unR, pR)) - Dn;
+  // 2 F(QL) + the wave sum (doublings on the integer pipe)
+  const double mL2 = scale_pow2<1>(QL[1]);
+  G[0] = mL2 + D0;
+  G[1] = fma(mL2, unL, fma(2.0, pL, Dn));
 #pragma unroll
-  for (int t = 0; t < NT; ++t) G[2 + t] = fma(QL[1], utL[t], QR[1] * utR[t]) - Dt[t];
-  G[E] = fma(unL, eL, unR * eR) - DE;
+  for (int t = 0; t < NT; ++t) G[2 + t] = fma(mL2, utL[t], Dt[t]);
+  G[E] = fma(scale_pow2<1>(unL), eL, DE);
 }
 
 // ------------------------------------------------------------ mbarrier / TMA (inline PTX)

@@ -10,7 +10,16 @@ max|ref|):
     precision reaches ~2e-12.  There the bar is 4x that measured oracle error,
     applied both to GPU - oracle and to GPU - extended precision, i.e. the GPU
     must be as accurate as the oracle;
-  * exact zero where the oracle's value is exactly zero (free stream).
+  * exact zero where the oracle's value is exactly zero (free stream);
+  * a residual is a sum of face-flux terms, and FP64 evaluations of it in
+    different operation orders differ by a few ulps of those terms (the GPU
+    flux uses refined reciprocals within 2 ulp, FMA contraction and a
+    rearranged, one-sided form), so the bar is never below 8 ulps of the
+    largest sum of the magnitudes of the terms (|F| ds over the cell's
+    faces, oracle.residual_terms).  That floor only matters where the
+    residual vanishes in exact arithmetic or nearly cancels (the unlimited
+    central scheme on the Taylor-Green vortex); elsewhere 1e-12 of max|R_v|
+    or 4x the oracle's error is the larger.
 Reconstruction is bitwise identical on both sides; the Roe flux differs by
 rounding order (FMA contraction, an algebraically rearranged flux, refined
 reciprocal square roots within 2 ulp).
@@ -31,6 +40,7 @@ pytestmark = pytest.mark.gpu
 
 TOL_RES = 1e-12
 TOL_100 = 1e-9
+EPS = np.finfo(np.float64).eps
 
 
 def relerr(a, b):
@@ -57,10 +67,12 @@ def assert_residual_parity(g, U, R, cells=None, tag="", s=None):
         Ro = O.residual(g, U, s).reshape(g.nvar, -1)
         Rx = O.residual_ext(g, U, s).reshape(g.nvar, -1)
         Rg = np.asarray(R).reshape(g.nvar, -1)
+        floor = 8 * EPS * O.residual_terms(g, U, s).reshape(g.nvar, -1).max(axis=1)
     else:
         Ro = O.residual_cells(g, U, cells).T
         Rx = O.residual_cells(g, U, cells, extended=True).T
         Rg = np.asarray(R).T
+        floor = np.zeros(g.nvar)
     report = []
     for v in range(g.nvar):
         scale = np.abs(Rx[v]).max()
@@ -70,7 +82,7 @@ def assert_residual_parity(g, U, R, cells=None, tag="", s=None):
         if scale == 0.0:
             assert d == 0.0 and np.all(Ro[v] == 0.0), (tag, v)
             continue
-        tol = max(TOL_RES * scale, 4.0 * e_orc)
+        tol = max(TOL_RES * scale, 4.0 * e_orc, floor[v])
         report.append(dict(var=v, rel_gpu_oracle=d / scale, rel_gpu_ext=e_gpu / scale, rel_oracle_ext=e_orc / scale))
         assert d <= tol, (tag, v, d / scale, e_orc / scale)
         assert e_gpu <= tol, (tag, v, e_gpu / scale, e_orc / scale)

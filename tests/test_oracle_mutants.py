@@ -32,8 +32,7 @@ MUTANTS = [
     ("MUSCL right state sign", "QR = q2 - e4 * sumR;", "QR = q2 + e4 * sumR;"),
     ("periodic ghost on the low side", "if (c < 0) return bc[0] == BC_PERIODIC ? ((c % n) + n) % n : 0;",
      "if (c < 0) return bc[0] == BC_PERIODIC ? 0 : 0;"),
-    ("residual sign", "+= (F[(size_t)v * nface + hi] - F[(size_t)v * nface + lo]) * ds;",
-     "+= (F[(size_t)v * nface + lo] - F[(size_t)v * nface + hi]) * ds;"),
+    ("residual sign", "R[(size_t)v * ncell + cidx] += (Fh - Fl) * ds;", "R[(size_t)v * ncell + cidx] += (Fl - Fh) * ds;"),
     ("face area of the wrong axis", "if (a != d) ds *= L.h[a];\n    int e[3]", "if (a == d) ds *= L.h[a];\n    int e[3]"),
     ("RK stage 2 weights", "U2[c] = 0.75 * U[c] + 0.25 * (", "U2[c] = 0.5 * U[c] + 0.5 * ("),
     ("RK stage 3 weights", "U[c] = (1.0 / 3.0) * U[c] + (2.0 / 3.0) * (", "U[c] = 0.5 * U[c] + 0.5 * ("),
