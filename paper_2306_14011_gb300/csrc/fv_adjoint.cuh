@@ -2,9 +2,10 @@
 // reconstruction, for the discrete adjoint of the residual (paper Eq. (5) with
 // the fluxes of Eq. (2) and states of Eq. (6)).
 //
-// roe_2F_vjp recomputes the forward quantities of roe_2F (fv_device.cuh) and
-// propagates a cotangent Gb of its output (2F) back to its inputs, line by
-// line in reverse.  Conventions at the non-differentiable points follow the
+// roe_2F_vjp recomputes the forward quantities of twice the flux of roe_F
+// (fv_device.cuh), in the central form (F(QL) + F(QR)) - sum |lambda| alpha r,
+// and propagates a cotangent Gb of that output (2F) back to its inputs, line
+// by line in reverse.  Conventions at the non-differentiable points follow the
 // forward-mode reference: |x| has derivative sign(x) with sign(+0) = +1, the
 // entropy fix takes the branch the forward pass took, and the limited slope
 // minmod(a, b) passes the derivative of the argument it returned (b on ties)
@@ -24,9 +25,9 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
                                            double efix, double inv2efix, const double (&Gb)[NT + 3],
                                            double (&QLb)[NT + 3], double (&QRb)[NT + 3]) {
   constexpr int E = NT + 2;
-  // ---------------- forward: the flux of roe_2F, with the Roe averages in
-  // their two-weight form u~ = wL uL + wR uR, H~ = wL HL + wR HR (the same
-  // function; roe_2F rearranges it to save FP64 operations)
+  // ---------------- forward: 2F in the central form, with the Roe averages
+  // in their two-weight form u~ = wL uL + wR uR, H~ = wL HL + wR HR (the same
+  // function as roe_F, which evaluates it one-sided to save FP64 operations)
   const double tL = rsqrt_fp64(QL[0]);
   const double rL = tL * tL;
   const double sL = QL[0] * tL;
@@ -82,7 +83,7 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   const double a2 = fma(-dp, ic2, QR[0] - QL[0]);
   const double x1 = un - c, x3 = un + c;
   const double m1 = iabs(x1), m3 = iabs(x3), l2 = iabs(un);
-  // the fix decision of roe_2F (FP32 copies), so both differentiate one function
+  // the fix decision of roe_F (FP32 copies), so both differentiate one function
   const float deltaf = __fmul_rn(f32_trunc(efix), f32_trunc(c));
   const bool fix1 = f32_trunc(m1) < deltaf, fix3 = f32_trunc(m3) < deltaf;
   double l1 = m1, l3 = m3, delta = 0.0, s2 = 0.0;

@@ -269,7 +269,7 @@ int split_stage(fv_ctx *c, int mode, const double *Us, const double *Un, double 
     double ds = 1.0;
     for (int e = 0; e < g.dim; ++e)
       if (e != d) ds *= h[e];
-    a.half_ds[d] = 0.5 * ds;
+    a.ds[d] = ds;
   }
   a.limiter = c->scheme.limiter;
   a.recon = c->scheme.recon;
@@ -324,8 +324,8 @@ int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, dou
     double ds = 1.0;  // area of a face normal to axis d
     for (int e = 0; e < g.dim; ++e)
       if (e != d) ds *= h[e];
-    a.half_ds[d] = 0.5 * ds;  // halved: the flux routine returns 2F
-    a.half_inv_h[d] = 0.5 / h[d];
+    a.ds[d] = ds;
+    a.inv_h[d] = (d < g.dim) ? g.n[d] / g.len[d] : 1.0;  // as the batched kernel's n / len
   }
   a.limiter = c->scheme.limiter;
   a.recon = c->scheme.recon;
@@ -459,14 +459,12 @@ int batch_setup(fv_ctx *c) {
       p.n[d] = G.n[d];
       p.ntile[d] = (G.n[d] + tile[d] - 1) / tile[d];
       const double h = G.len[d] / G.n[d];
-      p.half_inv_h[d] = 0.5 / h;
       p.inv_h[d] = G.n[d] / G.len[d];
       p.inv_hf[d] = (float)p.inv_h[d];
     }
     // the FP32 pre-selection's conditions (as for single grids)
     p.bounded = c->scheme.gamma < 1e6 && c->scheme.gamma - 1.0 >= 0x1p-20 && p.inv_h[0] >= 0x1p-30 &&
                 p.inv_h[0] <= 0x1p30 && p.inv_h[1] >= 0x1p-30 && p.inv_h[1] <= 0x1p30;
-    p.half_inv_h[2] = 0.5;
     for (int d = 0; d < 3; ++d) {
       p.bc[d][0] = G.bc[d][0];
       p.bc[d][1] = G.bc[d][1];
@@ -1031,7 +1029,7 @@ int adjoint(fv_ctx *c, const double *U, const double *lam, double *out, double w
   double h[3];
   for (int d = 0; d < 3; ++d) h[d] = (d < g.dim) ? g.len[d] / g.n[d] : 1.0;
   for (int d = 0; d < 3; ++d) {
-    if (w_dt == 0.0) {  // residual: face area / 2 (the flux routine's output is 2F)
+    if (w_dt == 0.0) {  // residual: face area / 2 (roe_2F_vjp differentiates 2F)
       double ds = 1.0;
       for (int e = 0; e < g.dim; ++e)
         if (e != d) ds *= h[e];

@@ -82,8 +82,8 @@ __device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double
     for (int d = 0; d < 3; ++d) {
       a.bc[d][0] = P.bc[d][0];
       a.bc[d][1] = P.bc[d][1];
-      a.half_ds[d] = 0.0;
-      a.half_inv_h[d] = P.half_inv_h[d];
+      a.ds[d] = 0.0;
+      a.inv_h[d] = d < 2 ? P.inv_h[d] : 0.0;
     }
     a.use_tma = 0;
     a.limiter = FV_LIM_MINMOD;

@@ -10,8 +10,8 @@
 //     rcp.approx.ftz.f64 / rsqrt.approx.ftz.f64 seeds (issued on the
 //     special-function unit, relative error below 2^-20) and are refined to
 //     full double precision by one third-order Householder step in FMA;
-//   * the Roe flux is arranged so each quantity is formed once and the 1/2 of
-//     the flux is folded into the caller's scale (roe_2F returns 2F).
+//   * the Roe flux is arranged so each quantity is formed once, and evaluated
+//     one-sided (roe_F), without the flux of the right state.
 #pragma once
 #include <cstdint>
 #include <cuda.h>
@@ -201,14 +201,13 @@ __device__ __forceinline__ bool wave_sum32(const double *U, long long N, long lo
 }
 
 // ------------------------------------------------------------ Roe flux
-// 2 min(x, 0) on the integer pipe: 2x for x < 0 (an exponent increment, see
-// scale_pow2), +0 for x >= 0 and for -0.
-__device__ __forceinline__ double twice_min0(double x) {
+// min(x, 0) on the integer pipe: x for x < 0, +0 for x >= 0 and for -0.
+__device__ __forceinline__ double min0(double x) {
   const bool neg = __double2hiint(x) < 0 && !izero(x);
-  return isel(neg, scale_pow2<1>(x), 0.0);
+  return isel(neg, x, 0.0);
 }
 
-// Twice the Roe flux across a face with unit normal along one axis.  States
+// The Roe flux across a face with unit normal along one axis.  States
 // are ordered normal-first: q = (rho, m_n, m_t[0..NT-1], rho*e_t), where m_n
 // is the momentum along the face normal and m_t the tangential momenta.
 // The flux is  F = (F(QL) + F(QR))/2 - sum_w |lambda_w| alpha_w r_w / 2
@@ -218,12 +217,13 @@ __device__ __forceinline__ double twice_min0(double x) {
 // delta^2)/(2 delta) for the acoustic waves when |lambda| < delta = efix c~.
 // Roe's averages make F(QR) - F(QL) = sum_w lambda_w alpha_w r_w exactly (in
 // exact arithmetic), so the same flux is evaluated one-sided, without F(QR):
-//   2F = 2 F(QL) + sum_w mu_w alpha_w r_w,   mu_w = lambda_w - |lambda_w|
-// (mu_w = 2 min(lambda_w, 0) on the integer pipe unless the fix applies).
-// Free streams give 2F(Q) exactly; fully supersonic faces give 2F(QL) exactly.
+//   F = F(QL) + sum_w mu_w alpha_w r_w,   mu_w = (lambda_w - |lambda_w|) / 2
+// (mu_w = min(lambda_w, 0), a select on the integer pipe, unless the fix
+// applies).  Free streams give F(Q) exactly; fully supersonic faces give
+// F(QL) exactly.
 // g1 = gamma - 1; inv2efix = 1 / (2 efix) (unused when efix = 0).
 template <int NT>
-__device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
+__device__ __forceinline__ void roe_F(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
                                        double efix, double inv2efix, double (&G)[NT + 3]) {
   constexpr int E = NT + 2;
   // left primitives: 1/sqrt(rho) gives both sqrt(rho) and 1/rho
@@ -287,23 +287,23 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   const double a3 = P2 + Q2;
   const double a2 = fma(-dp, ic2, drho);
 
-  // mu_w = lambda_w - |lambda_w|, with the entropy fix.  Whether |lambda| <
+  // mu_w = (lambda_w - |lambda_w|) / 2, with the entropy fix.  Whether |lambda| <
   // delta = efix c~ is decided in FP32 (operands truncated on the integer
   // pipe): the fixed |lambda| equals delta at |lambda| = delta, so a decision
   // flipped within FP32 resolution changes the flux by
   // O(((|lambda| - delta) / delta)^2 delta), below FP64 rounding.
   const double lam1 = un - c, lam3 = un + c;
-  double m1 = twice_min0(lam1), m3 = twice_min0(lam3);
-  const double m2 = twice_min0(un);
+  double m1 = min0(lam1), m3 = min0(lam3);
+  const double m2 = min0(un);
   const float deltaf = __fmul_rn(f32_trunc(efix), f32_trunc(c));
   const bool fix1 = f32_trunc(iabs(lam1)) < deltaf, fix3 = f32_trunc(iabs(lam3)) < deltaf;
   // near sonic points only: a warp-uniform branch keeps the (rare) fix from
   // being computed unconditionally
   if (__any_sync(__activemask(), fix1 || fix3)) {
     const double delta = efix * c;
-    const double d2 = delta * delta, s2 = tc * inv2efix;  // s2 = 1 / (2 delta)
-    m1 = isel(fix1, fma(-fma(lam1, lam1, d2), s2, lam1), m1);
-    m3 = isel(fix3, fma(-fma(lam3, lam3, d2), s2, lam3), m3);
+    const double d2 = delta * delta, s4 = 0.5 * (tc * inv2efix);  // s4 = 1 / (4 delta)
+    m1 = isel(fix1, fma(-fma(lam1, lam1, d2), s4, 0.5 * lam1), m1);
+    m3 = isel(fix3, fma(-fma(lam3, lam3, d2), s4, 0.5 * lam3), m3);
   }
 
   // sum_w mu_w alpha_w r_w
@@ -323,13 +323,12 @@ __device__ __forceinline__ void roe_2F(const double (&QL)[NT + 3], const double 
   }
   DE = fma(H, s13, fma(un, cd13, DE));
 
-  // 2 F(QL) + the wave sum (doublings on the integer pipe)
-  const double mL2 = scale_pow2<1>(QL[1]);
-  G[0] = mL2 + D0;
-  G[1] = fma(mL2, unL, fma(2.0, pL, Dn));
+  // F(QL) + the wave sum
+  G[0] = QL[1] + D0;
+  G[1] = fma(QL[1], unL, pL + Dn);
 #pragma unroll
-  for (int t = 0; t < NT; ++t) G[2 + t] = fma(mL2, utL[t], Dt[t]);
-  G[E] = fma(scale_pow2<1>(unL), eL, DE);
+  for (int t = 0; t < NT; ++t) G[2 + t] = fma(QL[1], utL[t], Dt[t]);
+  G[E] = fma(unL, eL, DE);
 }
 
 // ------------------------------------------------------------ mbarrier / TMA (inline PTX)

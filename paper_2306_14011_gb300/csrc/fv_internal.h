@@ -41,8 +41,8 @@ struct StageArgs {
   double half_eps;     // eps / 2 (MUSCL slope weight)
   double efix;         // entropy-fix width / c~
   double inv2efix;     // 1 / (2 efix), 0 when efix = 0
-  double half_ds[3];   // residual mode: face area / 2 per axis
-  double half_inv_h[3];  // stage modes: 1 / (2 dx_d)
+  double ds[3];        // residual mode: face area per axis
+  double inv_h[3];     // stage modes: 1 / dx_d
   const unsigned long long *smax;  // CFL mode: bits of max wave-speed sum, else null
   double cfl;          // CFL number (with smax)
   double dt_fixed;     // step when smax is null
@@ -73,7 +73,6 @@ struct BatchProblem {
   int n[2];              // cells along x, y
   int ntile[2];          // tiles along x, y
   int bc[3][2];          // FV_BC_* per axis side
-  double half_inv_h[3];  // 1 / (2 dx_d)
   double inv_h[2];       // 1 / dx_d
   float inv_hf[2];       // 1 / dx_d in FP32 (time-step pre-selection)
   int bounded;           // 1: FP32 pre-selection of the time-step reduction applies
@@ -97,8 +96,8 @@ struct BatchArgs {
 };
 
 // The split kernel structure (fv_launch.mode = FV_SPLIT): per axis a limiter
-// kernel writing the MUSCL face states QL, QR and a flux kernel writing 2F
-// (the Roe routine's output), then source, right-hand-side and update
+// kernel writing the MUSCL face states QL, QR and a flux kernel writing the
+// Roe flux F, then source, right-hand-side and update
 // kernels.  Face arrays of axis d are [nvar][nface[d]] with faces indexed x
 // fastest over (n[0] + (d == 0)) x (n[1] + (d == 1)) x (n[2] + (d == 2)); face
 // m along d lies between cells m - 1 and m.
@@ -112,14 +111,14 @@ struct SplitArgs {
   const double *Un;          // U^n for stages 2 and 3
   double *out;               // the next stage state (stage modes)
   double *QL[3], *QR[3];     // face states per axis
-  double *F[3];              // 2F per axis
+  double *F[3];              // Roe flux per axis
   double *R;                 // the residual (the output in residual mode)
   double *norm_part;         // residual mode: per-CTA partial sums of R_v^2 of the RHS kernel, or null
   const double *S;           // source of Eq. (5), or null
   double vol, inv_vol;       // |Omega| and 1 / |Omega|
   int limiter, recon;        // FV_LIM_*, FV_RECON_*
   double inv_g1, cL, cR, g1, half_eps, efix, inv2efix;
-  double half_ds[3];         // face area / 2 per axis
+  double ds[3];              // face area per axis
   const unsigned long long *smax;  // CFL mode: bits of the max wave-speed sum, else null
   double cfl, dt_fixed;
   double *t_acc;             // stage 3: simulated time (one thread adds dt), or null

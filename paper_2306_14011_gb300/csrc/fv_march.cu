@@ -123,7 +123,7 @@ __device__ __forceinline__ void march_face(const double *p0, const double *p1, c
   }
   qL[4] = QL[4];
   qR[4] = QR[4];
-  roe_2F<2>(qL, qR, a.g1, a.efix, a.inv2efix, Gf);
+  roe_F<2>(qL, qR, a.g1, a.efix, a.inv2efix, Gf);
   F[f] = Gf[0];
   F[(1 + D) * fs + f] = Gf[1];
   t = 0;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
     }
     s_coef[0] = dt;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) s_coef[1 + d] = (MODE == MODE_RESIDUAL) ? a.half_ds[d] : -w * dt * a.half_inv_h[d];
+    for (int d = 0; d < 3; ++d) s_coef[1 + d] = (MODE == MODE_RESIDUAL) ? a.ds[d] : -w * dt * a.inv_h[d];
     s_coef[4] = (MODE == MODE_RESIDUAL) ? -a.vol : w * dt;
   }
   __syncthreads();

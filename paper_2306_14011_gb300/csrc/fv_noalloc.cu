@@ -137,8 +137,8 @@ extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const d
     double ds = 1.0;
     for (int e = 0; e < g->dim; ++e)
       if (e != d) ds *= h[e];
-    a.half_ds[d] = 0.5 * ds;
-    a.half_inv_h[d] = 0.5 / h[d];
+    a.ds[d] = ds;
+    a.inv_h[d] = (d < g->dim) ? g->n[d] / g->len[d] : 1.0;  // as the batched kernel's n / len
   }
   a.use_tma = 0;  // plain loads: no tensor map, results identical to the TMA loader
   a.march = k.march;

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kSplitMaxThreads) limiter_kernel(const SplitAr
   }
 }
 
-// Flux kernel of axis D: 2F of the Roe flux at every face normal to D.
+// Flux kernel of axis D: the Roe flux at every face normal to D.
 template <int DIM, int D>
 __global__ void __launch_bounds__(kSplitMaxThreads) flux_kernel(const SplitArgs a) {
   constexpr int NV = DIM + 2, NT = DIM - 1, E = NV - 1;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kSplitMaxThreads) flux_kernel(const SplitArgs 
     }
     qL[E] = QL[E];
     qR[E] = QR[E];
-    roe_2F<NT>(qL, qR, a.g1, a.efix, a.inv2efix, G);
+    roe_F<NT>(qL, qR, a.g1, a.efix, a.inv2efix, G);
     double *F = a.F[D];
     F[f] = G[0];
     F[(1 + D) * nf + f] = G[1];
@@ -125,9 +125,8 @@ __global__ void __launch_bounds__(kSplitMaxThreads) source_kernel(const SplitArg
   }
 }
 
-// Right-hand-side kernel: R += sum_d ds_d (F_{m+1/2} - F_{m-1/2}) per cell
-// (2F stored, so half the face area), axes in order; optional per-CTA sums of
-// R_v^2 (lanes, then warps).
+// Right-hand-side kernel: R += sum_d ds_d (F_{m+1/2} - F_{m-1/2}) per cell,
+// axes in order; optional per-CTA sums of R_v^2 (lanes, then warps).
 template <int DIM>
 __global__ void __launch_bounds__(kSplitMaxThreads) rhs_kernel(const SplitArgs a) {
   constexpr int NV = DIM + 2;
@@ -153,7 +152,7 @@ __global__ void __launch_bounds__(kSplitMaxThreads) rhs_kernel(const SplitArgs a
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         const double *F = a.F[d] + v * a.nface[d];
-        r = fma(a.half_ds[d], F[flo[d] + fst[d]] - F[flo[d]], r);
+        r = fma(a.ds[d], F[flo[d] + fst[d]] - F[flo[d]], r);
       }
       a.R[v * N + c] = r;
       if (a.norm_part) nrm[v] = fma(r, r, nrm[v]);

@@ -254,7 +254,7 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
       }
       qL[E] = QL[E];
       qR[E] = QR[E];
-      roe_2F<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gf);
+      roe_F<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gf);
       F[f] = Gf[0];
       F[(1 + D) * G.fmax + f] = Gf[1];
       t = 0;
@@ -370,7 +370,7 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
     }
     s_coef[0] = dt;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) s_coef[1 + d] = (MODE == MODE_RESIDUAL) ? a.half_ds[d] : -w * dt * a.half_inv_h[d];
+    for (int d = 0; d < 3; ++d) s_coef[1 + d] = (MODE == MODE_RESIDUAL) ? a.ds[d] : -w * dt * a.inv_h[d];
     s_coef[4] = (MODE == MODE_RESIDUAL) ? -a.vol : w * dt;
   }
   __syncthreads();
