@@ -54,6 +54,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # step), valid for the kernel sources whose hash and the launch shape recorded
 # with it; null otherwise.
 STAGE_TRAFFIC = {"bytes": 1.3904e9, "source_hash": "b0cc6bae41c6af4b", "tile": [32, 32, 1], "threads": 160}
+# FP64 instructions the fused stage kernels execute per cell and stage (ncu
+# sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on, mean of the three
+# stages at 2048^2 / 192^3), for the kernel sources with this hash.
+STAGE_FP64_INST = {"2d": 217.7, "3d": 412.5, "source_hash": "b0cc6bae41c6af4b"}
 
 
 def kernel_source_hash() -> str:
@@ -285,6 +289,17 @@ def run_ours(args):
         "clocks": clk,
         "impl": "ours",
     }
+    if not W["batched"] and not split:
+        # the kernel's FP64 instruction rate against a DFMA stream kernel on
+        # the same device and clock (the issue-rate ceiling in practice)
+        stream_rate = fv.fv_debug_fp64_rate(0)
+        inst = STAGE_FP64_INST["2d" if g.dim == 2 else "3d"]
+        if STAGE_FP64_INST["source_hash"] != kernel_source_hash():
+            inst = None
+        rate = inst * cells / (stage_ms / 1e3) if inst else None
+        line["roofline"]["fp64_stream"] = {
+            "dfma_stream_lane_ops_per_s": stream_rate, "kernel_fp64_inst_per_cell_stage": inst,
+            "kernel_fp64_lane_ops_per_s": rate, "frac_of_stream": rate / stream_rate if rate else None}
     if args.workload != "kh4096":
         line["metric"] = W["metric"]
     if args.tune and not W["batched"]:

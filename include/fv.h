@@ -376,6 +376,15 @@ int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const double *U, d
  * precision).  Stream-ordered on `stream`. */
 int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, void *stream);
 
+/* Reference FP64 issue rate of the current device (not in the paper; for
+ * reporting the ALU roofline): a kernel of 8 x SMs CTAs of 256 threads, each
+ * thread running 8 independent chains of 4096 DFMA (kind 0) or DADD (kind 1)
+ * operations, timed with CUDA events on `stream` after a short warm-up.
+ * *lane_ops_per_s receives FP64 operations (lanes) per second.  Allocates
+ * and frees 256 doubles per CTA; synchronises `stream`.  FV_EINVAL for a bad
+ * kind or a NULL output. */
+int fv_debug_fp64_rate(int kind, double *lane_ops_per_s, void *stream);
+
 /* The kernels' integer-pipe replacements of FP64 operations, applied to n
  * device doubles (for tests): out[i] = op(x[i], y[i]) with op 0: x/2 for
  * x >= 0 (half_nonneg), 1: x/4, 2: x/2, 3: 2x (exponent shifts), 4:

@@ -1126,6 +1126,33 @@ int fv_debug_bits(int op, const double *x, const double *y, double *out, long n,
   return FV_OK;
 }
 
+int fv_debug_fp64_rate(int kind, double *lane_ops_per_s, void *stream) {
+  if ((kind != 0 && kind != 1) || !lane_ops_per_s) return FV_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  FV_CK(cudaGetDevice(&dev));
+  FV_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = 8 * sms, iters = 4096;  // 2048 threads per SM, ~20 ms
+  double *out = nullptr;
+  FV_CK(cudaMalloc(&out, sizeof(double) * 256 * (size_t)blocks));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int r = FV_OK;
+  float ms = 0.f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      launch_fp64_stream(kind, blocks, iters / 8, out, st) != cudaSuccess ||  // warm-up
+      cudaEventRecord(e0, st) != cudaSuccess || launch_fp64_stream(kind, blocks, iters, out, st) != cudaSuccess ||
+      cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    r = FV_ECUDA;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (r == FV_OK) *lane_ops_per_s = (double)blocks * 256 * iters * 8 / (1e-3 * ms);
+  return r;
+}
+
 int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, void *stream) {
   if (!x || !out_rsqrt || !out_rcp || n < 0) return FV_EINVAL;
   FV_CK(launch_debug_math(x, out_rsqrt, out_rcp, n, static_cast<cudaStream_t>(stream)));

@@ -165,6 +165,8 @@ cudaError_t launch_dt(const DtArgs &a, int blocks, int threads, cudaStream_t st)
 cudaError_t launch_dt_finalize(const unsigned long long *smax, double cfl, double *out, cudaStream_t st);
 cudaError_t launch_norm_finalize(const double *part, int nparts, int nvar, double *out, cudaStream_t st);
 cudaError_t launch_debug_math(const double *x, double *o1, double *o2, long n, cudaStream_t st);
+// blocks x 256 threads, 8 chains of `iters` DFMA (kind 0) / DADD (kind 1) each; out: blocks x 256 doubles.
+cudaError_t launch_fp64_stream(int kind, int blocks, int iters, double *out, cudaStream_t st);
 cudaError_t launch_debug_bits(int op, const double *x, const double *y, double *out, long n, cudaStream_t st);
 cudaError_t launch_debug_wait(int kind, unsigned long long limit_ns, unsigned *word, unsigned *flags,
                               cudaStream_t st);

@@ -244,6 +244,28 @@ cudaError_t launch_debug_bits(int op, const double *x, const double *y, double *
   return cudaGetLastError();
 }
 
+// FP64 issue-rate reference: every thread runs 8 independent chains of
+// `iters` DFMA (kind 0) or DADD (kind 1) operations; out receives one sum
+// per thread so nothing is optimised away.
+__global__ void __launch_bounds__(256) fp64_stream_kernel(int kind, double a, double b, int iters, double *out) {
+  double x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = a + threadIdx.x * 1e-9 + i;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = kind == 0 ? fma(x[i], a, b) : x[i] + b;
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += x[i];
+  out[(long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t launch_fp64_stream(int kind, int blocks, int iters, double *out, cudaStream_t st) {
+  fp64_stream_kernel<<<blocks, 256, 0, st>>>(kind, 1.0000001, 1e-7, iters, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_debug_math(const double *x, double *o1, double *o2, long n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   long blocks = (n + 255) / 256;

@@ -121,6 +121,8 @@ def load() -> C.CDLL:
         L.fv_debug_wait.argtypes = [C.c_int, C.c_double, _VP]
         L.fv_debug_wait.restype = C.c_int
         L.fv_debug_bits.argtypes = [C.c_int, _VP, _VP, _VP, C.c_long, _VP]
+        L.fv_debug_fp64_rate.argtypes = [C.c_int, P(C.c_double), _VP]
+        L.fv_debug_fp64_rate.restype = C.c_int
         L.fv_debug_bits.restype = C.c_int
         L.fv_layout.argtypes = [_VP, P(C.c_longlong), C.c_int]
         L.fv_layout.restype = C.c_int
@@ -386,6 +388,14 @@ def fv_debug_bits(op: int, x, out, y=None, stream=None):
     """out = op(x[, y]) with the kernels' integer-pipe helpers (see fv.h)."""
     _check(load().fv_debug_bits(int(op), _ptr(x), None if y is None else _ptr(y), _ptr(out), x.numel(),
                                 _stream_handle(stream)), "fv_debug_bits")
+
+
+def fv_debug_fp64_rate(kind: int = 0, stream=None) -> float:
+    """FP64 lane-operations per second of a DFMA (kind 0) or DADD (kind 1)
+    stream kernel filling the device: the reference issue rate."""
+    r = C.c_double(0.0)
+    _check(load().fv_debug_fp64_rate(int(kind), C.byref(r), _stream_handle(stream)), "fv_debug_fp64_rate")
+    return r.value
 
 
 def fv_debug_math(x, out_rsqrt, out_rcp, stream=None):

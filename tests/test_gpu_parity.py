@@ -301,6 +301,19 @@ def test_invalid_launch_is_rejected():
         assert e.value.status == fv.FV_EINVAL
 
 
+def test_fp64_stream_rate_is_below_the_unit_count_peak():
+    """The reference FP64 issue rate (DFMA and DADD streams) lies between 60%
+    and 100% of 2 lanes per clock per SM at the device's maximum clock."""
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    clk_hz = 2.07e9 if "GB300" in props.name else None
+    for kind in (0, 1):
+        r = fv.fv_debug_fp64_rate(kind)
+        assert r > 0
+        if clk_hz:
+            assert 0.6 <= r / (2 * sms * clk_hz) <= 1.0, r
+
+
 def test_refined_rsqrt_and_reciprocal_are_within_two_ulp():
     rng = np.random.default_rng(0)
     x = np.exp2(rng.uniform(-300, 300, 1 << 20)) * rng.uniform(1, 2, 1 << 20)

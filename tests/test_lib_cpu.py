@@ -105,6 +105,12 @@ def test_tuning_space_sizes():
             fv.fv_tune_space(dim, mode)
 
 
+def test_fp64_rate_rejects_bad_arguments_on_the_host():
+    lib = fv.load()
+    assert lib.fv_debug_fp64_rate(2, C.byref(C.c_double()), None) == fv.FV_EINVAL
+    assert lib.fv_debug_fp64_rate(0, None, None) == fv.FV_EINVAL
+
+
 def test_debug_wait_rejects_bad_arguments_on_the_host():
     for kind, limit in [(2, 0.1), (-1, 0.1), (0, 0.0), (1, -1.0), (0, 11.0), (1, float("nan"))]:
         with pytest.raises(fv.FvError) as e:
