@@ -72,8 +72,9 @@ enum { FV_RECON_CONSERVED = 0, FV_RECON_PRIMITIVE = 1 };
  * order, 1 central).  With either limiter the two kappa-weighted limited
  * slopes are equal, so kappa matters only for FV_LIM_NONE.  Batched contexts
  * and the adjoint support FV_LIM_MINMOD only.
- * efix: Harten entropy-fix width as a fraction of the Roe sound speed (0.1);
- * 0 disables the fix.
+ * efix: Harten entropy-fix width as a fraction of the Roe sound speed (0.1),
+ * 0 <= efix < 1 (the fix stays within one acoustic wave's sonic region); 0
+ * disables the fix.
  * recon: the variables Eq. (6) extrapolates -- FV_RECON_CONSERVED (Sec. 3.1,
  * the default) or FV_RECON_PRIMITIVE (rho, velocity, p; the face states are
  * converted back to conserved variables for the flux).  Primitive

@@ -133,7 +133,8 @@ int validate_grid(const fv_grid *g) {
 }
 
 int validate_scheme(const fv_scheme *s) {
-  if (!s || !(s->gamma > 1.0) || !(s->cfl > 0.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0))
+  if (!s || !(s->gamma > 1.0) || !(s->cfl > 0.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0) ||
+      !(s->efix < 1.0))
     return FV_EINVAL;
   if (s->limiter != FV_LIM_MINMOD && s->limiter != FV_LIM_VANLEER && s->limiter != FV_LIM_NONE) return FV_EINVAL;
   if (s->recon != FV_RECON_CONSERVED && s->recon != FV_RECON_PRIMITIVE) return FV_EINVAL;

@@ -207,24 +207,35 @@ __device__ __forceinline__ double min0(double x) {
   return isel(neg, x, 0.0);
 }
 
-// The Roe flux across a face with unit normal along one axis.  States
-// are ordered normal-first: q = (rho, m_n, m_t[0..NT-1], rho*e_t), where m_n
-// is the momentum along the face normal and m_t the tangential momenta.
+// -x by flipping the sign bit (integer pipe).
+__device__ __forceinline__ double ineg(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
+}
+
+// The Roe flux across a face with unit normal along one axis.  States are
+// ordered normal-first: q = (rho, m_n, m_t[0..NT-1], rho*e_t), where m_n is
+// the momentum along the face normal and m_t the tangential momenta.
 // The flux is  F = (F(QL) + F(QR))/2 - sum_w |lambda_w| alpha_w r_w / 2
 // with acoustic waves alpha_{1,3} = (dp -+ rho~ c~ du_n) / (2 c~^2), entropy
 // wave alpha_2 = drho - dp / c~^2, shear waves rho~ du_t, eigenvalues
 // u~_n -+ c~ and u~_n; Harten's fix replaces |lambda| by (lambda^2 +
 // delta^2)/(2 delta) for the acoustic waves when |lambda| < delta = efix c~.
 // Roe's averages make F(QR) - F(QL) = sum_w lambda_w alpha_w r_w exactly (in
-// exact arithmetic), so the same flux is evaluated one-sided, without F(QR):
-//   F = F(QL) + sum_w mu_w alpha_w r_w,   mu_w = (lambda_w - |lambda_w|) / 2
-// (mu_w = min(lambda_w, 0), a select on the integer pipe, unless the fix
-// applies).  Free streams give F(Q) exactly; fully supersonic faces give
-// F(QL) exactly.
-// g1 = gamma - 1; inv2efix = 1 / (2 efix) (unused when efix = 0).
+// exact arithmetic), so
+//   F = F(QL) + sum_w (lambda_w - |lambda_w|)/2 alpha_w r_w
+//     = F(QR) - sum_w (lambda_w + |lambda_w|)/2 alpha_w r_w.
+// Taken from the upwind side of u~_n, every wave but one acoustic wave drops
+// out: for u~_n >= 0 the entropy, shear and u~_n + c~ waves have lambda >= 0
+// and (efix < 1) |lambda| >= c~ > delta, so only the u~_n - c~ wave is left;
+// for u~_n < 0 symmetrically only u~_n + c~.  With x = |u~_n| - c~,
+//   F = F(Q_upwind) + k alpha_s r_s,   k = (x - |x|*)/2  (= min(x, 0)),
+// alpha_s = dp/(2 c~^2) -+ rho~ du_n/(2 c~), r_s = (1, u~_n -+ c~, u~_t,
+// H~ - c~ |u~_n|) (upper signs for u~_n >= 0).  Free streams give F(Q)
+// exactly; fully supersonic faces give the upwind physical flux exactly.
+// g1 = gamma - 1; inv2efix = 1 / (2 efix) (unused when efix = 0); efix < 1.
 template <int NT>
 __device__ __forceinline__ void roe_F(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
-                                       double efix, double inv2efix, double (&G)[NT + 3]) {
+                                      double efix, double inv2efix, double (&G)[NT + 3]) {
   constexpr int E = NT + 2;
   // left primitives: 1/sqrt(rho) gives both sqrt(rho) and 1/rho
   const double tL = rsqrt_fp64(QL[0]);
@@ -256,79 +267,56 @@ __device__ __forceinline__ void roe_F(const double (&QL)[NT + 3], const double (
   const double eR = QR[E] + pR;
 
   // Roe averages with sqrt(rho) weights wL = sL / (sL + sR), wR = 1 - wL:
-  // u~ = uR - wL (uR - uL) reuses the velocity jumps of the wave strengths,
-  // and H~ = (sL HL + sR HR) / (sL + sR) with sL HL = eL / sL = eL tL
+  // u~ = uR - wL (uR - uL), and H~ = (sL HL + sR HR) / (sL + sR) with
+  // sL HL = eL / sL = eL tL
   const double inv = rcp_fp64(sL + sR);
   const double wL = sL * inv;
   const double dun = unR - unL;
   const double un = fma(-wL, dun, unR);
-  double ut[NT], dut[NT];
+  double ut[NT];
   double q2 = un * un;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    dut[t] = utR[t] - utL[t];
-    ut[t] = fma(-wL, dut[t], utR[t]);
+    ut[t] = fma(-wL, utR[t] - utL[t], utR[t]);
     q2 = fma(ut[t], ut[t], q2);
   }
   const double H = fma(eL, tL, eR * tR) * inv;
   const double rho = sL * sR;
-  const double hq = half_nonneg(q2);
-  const double c2 = g1 * (H - hq);
+  const double c2 = g1 * (H - half_nonneg(q2));
   const double tc = rsqrt_fp64(c2);  // 1/c~
   const double c = c2 * tc;
-  const double ic2 = tc * tc;        // 1/c~^2
 
-  // wave strengths alpha_{1,3} = dp / (2 c~^2) -+ rho~ du_n / (2 c~)
-  const double drho = QR[0] - QL[0];
+  // the acoustic wave that crosses from downwind (upper signs: u~_n >= 0)
+  const bool up_left = __double2hiint(un) >= 0;
+  const double aun = iabs(un);
+  const double sc = isel(up_left, c, ineg(c));
   const double dp = pR - pL;
-  const double P2 = dp * half_nonneg(ic2);
-  const double Q2 = (rho * dun) * half_nonneg(tc);
-  const double a1 = P2 - Q2;
-  const double a3 = P2 + Q2;
-  const double a2 = fma(-dp, ic2, drho);
-
-  // mu_w = (lambda_w - |lambda_w|) / 2, with the entropy fix.  Whether |lambda| <
-  // delta = efix c~ is decided in FP32 (operands truncated on the integer
-  // pipe): the fixed |lambda| equals delta at |lambda| = delta, so a decision
-  // flipped within FP32 resolution changes the flux by
-  // O(((|lambda| - delta) / delta)^2 delta), below FP64 rounding.
-  const double lam1 = un - c, lam3 = un + c;
-  double m1 = min0(lam1), m3 = min0(lam3);
-  const double m2 = min0(un);
+  const double alpha = (fma(-(rho * sc), dun, dp) * tc) * half_nonneg(tc);  // (dp -+ rho~ c~ du_n) / (2 c~^2)
+  const double x = aun - c;
+  // k = (x - |x|*)/2 with the entropy fix.  Whether |x| < delta = efix c~ is
+  // decided in FP32 (operands truncated on the integer pipe): the fixed |x|
+  // equals delta at |x| = delta, so a decision flipped within FP32
+  // resolution changes the flux by O(((|x| - delta) / delta)^2 delta), below
+  // FP64 rounding.  Near sonic points only: a warp-uniform branch keeps the
+  // (rare) fix from being computed unconditionally.
+  double k = min0(x);
   const float deltaf = __fmul_rn(f32_trunc(efix), f32_trunc(c));
-  const bool fix1 = f32_trunc(iabs(lam1)) < deltaf, fix3 = f32_trunc(iabs(lam3)) < deltaf;
-  // near sonic points only: a warp-uniform branch keeps the (rare) fix from
-  // being computed unconditionally
-  if (__any_sync(__activemask(), fix1 || fix3)) {
+  const bool fix = f32_trunc(iabs(x)) < deltaf;
+  if (__any_sync(__activemask(), fix)) {
     const double delta = efix * c;
     const double d2 = delta * delta, s4 = 0.5 * (tc * inv2efix);  // s4 = 1 / (4 delta)
-    m1 = isel(fix1, fma(-fma(lam1, lam1, d2), s4, 0.5 * lam1), m1);
-    m3 = isel(fix3, fma(-fma(lam3, lam3, d2), s4, 0.5 * lam3), m3);
+    k = isel(fix, fma(-fma(x, x, d2), s4, 0.5 * x), k);
   }
+  const double g = k * alpha;
 
-  // sum_w mu_w alpha_w r_w
-  const double A1 = m1 * a1, A2 = m2 * a2, A3 = m3 * a3;
-  const double lr = m2 * rho;
-  const double s13 = A1 + A3;
-  const double cd13 = c * (A3 - A1);
-  const double D0 = s13 + A2;
-  const double Dn = fma(un, D0, cd13);
-  double DE = hq * A2;
-  double Dt[NT];
+  // F(Q_upwind) + g r_s (selects on the integer pipe)
+  const double m = isel(up_left, QL[1], QR[1]);
+  const double u_n = isel(up_left, unL, unR);
+  G[0] = m + g;
+  G[1] = fma(m, u_n, isel(up_left, pL, pR) + g * (un - sc));
 #pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    const double B = lr * dut[t];
-    Dt[t] = fma(ut[t], D0, B);
-    DE = fma(ut[t], B, DE);
-  }
-  DE = fma(H, s13, fma(un, cd13, DE));
-
-  // F(QL) + the wave sum
-  G[0] = QL[1] + D0;
-  G[1] = fma(QL[1], unL, pL + Dn);
-#pragma unroll
-  for (int t = 0; t < NT; ++t) G[2 + t] = fma(QL[1], utL[t], Dt[t]);
-  G[E] = fma(unL, eL, DE);
+  for (int t = 0; t < NT; ++t) G[2 + t] = fma(m, isel(up_left, utL[t], utR[t]), g * ut[t]);
+  G[E] = fma(u_n, isel(up_left, eL, eR), g * fma(-c, aun, H));
 }
 
 // ------------------------------------------------------------ mbarrier / TMA (inline PTX)

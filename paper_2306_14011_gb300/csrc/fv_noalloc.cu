@@ -89,7 +89,7 @@ bool grid_ok(const fv_grid *g) {
 extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const double *U, double *R,
                                    double *rnorm2, void *stream) {
   if (!grid_ok(g) || !s || !(s->gamma > 1.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0) ||
-      s->limiter < FV_LIM_MINMOD || s->limiter > FV_LIM_NONE ||
+      !(s->efix < 1.0) || s->limiter < FV_LIM_MINMOD || s->limiter > FV_LIM_NONE ||
       (s->recon != FV_RECON_CONSERVED && s->recon != FV_RECON_PRIMITIVE))
     return FV_EINVAL;
   if (!U || !R || U == R || !device_pointer(U) || !device_pointer(R) || (rnorm2 && !device_pointer(rnorm2)))
