@@ -289,8 +289,10 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
       for (int v = 0; v < NV3; ++v) {
         // same accumulation as the box-tiled kernel: the stage base, then x, y, z
         const double dFx = Fx[v * G.nfx + fx + 1] - Fx[v * G.nfx + fx];
-        double rv = (MODE == MODE_RESIDUAL && !a.S) ? cx * dFx
-                                                    : fma(cx, dFx, start_value<MODE>(a, cur[v * G.plane + lc], v * N + gi, src));
+        const double un = (MODE == MODE_STAGE2 || MODE == MODE_STAGE3) ? a.Un[v * N + gi] : 0.0;
+        double rv = (MODE == MODE_RESIDUAL && !a.S)
+                        ? cx * dFx
+                        : fma(cx, dFx, start_value<MODE>(a, cur[v * G.plane + lc], un, v * N + gi, src));
         rv = fma(cy, Fy[v * G.nfy + fy + ext0] - Fy[v * G.nfy + fy], rv);
         rv = fma(cz, Fzc[v * G.cols + c] - Fzp[v * G.cols + c], rv);
         if (MODE == MODE_RESIDUAL && want_norm) nrm[v] = fma(rv, rv, nrm[v]);

@@ -158,19 +158,19 @@ __device__ __forceinline__ void box_to_primitive(double *tile, const TileGeom &G
 // The part of a stage update that does not depend on the fluxes: Us (stage
 // 1), 3/4 Un + 1/4 Us (stage 2), 1/3 Un + 2/3 Us (stage 3); 0 for the residual.
 template <int MODE>
-__device__ __forceinline__ double stage_base(double us, const double *un) {
+__device__ __forceinline__ double stage_base(double us, double un) {
   if (MODE == MODE_RESIDUAL) return 0.0;
   if (MODE == MODE_STAGE1) return us;
-  if (MODE == MODE_STAGE2) return fma(0.75, *un, quarter(us));
-  return fma(1.0 / 3.0, *un, (2.0 / 3.0) * us);
+  if (MODE == MODE_STAGE2) return fma(0.75, un, quarter(us));
+  return fma(1.0 / 3.0, un, (2.0 / 3.0) * us);
 }
 
 // The value a cell's accumulation starts from: the stage base, plus the
 // source term of Eq. (5) when one is set (src = -|Omega| for the residual,
 // w dt for an RK stage, since dU/dt = -R/|Omega| has +S).
 template <int MODE>
-__device__ __forceinline__ double start_value(const StageArgs &a, double us, long long idx, double src) {
-  double b = stage_base<MODE>(us, a.Un + idx);
+__device__ __forceinline__ double start_value(const StageArgs &a, double us, double un, long long idx, double src) {
+  double b = stage_base<MODE>(us, un);
   if (a.S) b = (MODE == MODE_RESIDUAL) ? src * a.S[idx] : fma(src, a.S[idx], b);
   return b;
 }
@@ -267,6 +267,7 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
       F[E * G.fmax + f] = Gf[E];
     }
   }
+  if (D == 0 && (MODE == MODE_STAGE2 || MODE == MODE_STAGE3)) cp_async_wait_all();  // this thread's U^n copies
   __syncthreads();
   // R accumulates the new value of each cell: the first axis starts from the
   // stage base (RK modes) or from 0 (residual), so the update needs no
@@ -292,9 +293,10 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
       if (D == 0) {
         if (MODE == MODE_RESIDUAL && !a.S)
           R[v * G.cells + c] = coef * dF;
-        else
+        else  // stages 2 and 3: R holds U^n, copied in by prefetch_un
           R[v * G.cells + c] =
               fma(coef, dF, start_value<MODE>(a, a.recon == FV_RECON_PRIMITIVE ? a.Us[v * N + gi] : tile[v * G.plane + lc],
+                                              (MODE == MODE_STAGE2 || MODE == MODE_STAGE3) ? R[v * G.cells + c] : 0.0,
                                               v * N + gi, src));
       } else {
         R[v * G.cells + c] = fma(coef, dF, R[v * G.cells + c]);
@@ -302,6 +304,29 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
     }
   }
   __syncthreads();
+}
+
+// Stages 2 and 3: U^n of the tile's cells into the accumulator R, with
+// asynchronous copies issued before the tile load completes, so their latency
+// hides behind the load and the first axis's fluxes; the first axis's
+// accumulation (same cell-to-thread map) waits for the thread's own copies and
+// reads U^n there before overwriting it.
+template <int DIM, int MODE>
+__device__ __forceinline__ void prefetch_un(double *R, const StageArgs &a, const int o[3], const int ext[3],
+                                            const TileGeom &G) {
+  if (MODE != MODE_STAGE2 && MODE != MODE_STAGE3) return;
+  constexpr int NV = DIM + 2;
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+  const int ncell = ext[0] * ext[1] * ext[2];
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = c % ext[0];
+    const int rr = c / ext[0];
+    const int j = rr % ext[1];
+    const int k = rr / ext[1];
+    const long long gi = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cp_async8(smem_u32(R + v * G.cells + c), a.Un + v * N + gi);
+  }
 }
 
 // All the work of one tile: stage the tile (TMA with mbarrier `bar` at parity
@@ -325,7 +350,7 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
   ext[2] = (DIM == 3) ? min(a.tile[2], a.n[2] - o[2]) : 1;
   const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
 
-  // ---- 1. stage the tile and its halo
+  // ---- 1. stage the tile and its halo (and, stages 2-3, U^n into R)
   if (a.use_tma) {
     const uint32_t bar = smem_u32(mbar);
     if (threadIdx.x == 0) {
@@ -335,8 +360,10 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
       else
         tma_load_4d(smem_u32(tile), tmap, o[0] - 2, o[1] - 2, o[2] - 2, 0, bar);
     }
+    prefetch_un<DIM, MODE>(R, a, o, ext, G);
     const bool ok = mbar_wait_bounded(bar, phase, kTmaWaitNs);
     if (__syncthreads_or(!ok)) {
+      if (MODE == MODE_STAGE2 || MODE == MODE_STAGE3) cp_async_wait_all();
       if (threadIdx.x == 0) {
         atomicOr(a.flags, FLAG_TIMEOUT);
         mbar_wait_bounded(bar, phase, kTmaWaitNs);  // let a late copy land before the CTA moves on
@@ -345,6 +372,7 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
     }
     load_halo<DIM>(tile, a, o, ext, G, true);
   } else {
+    prefetch_un<DIM, MODE>(R, a, o, ext, G);
     const int ncell = ext[0] * ext[1] * ext[2];
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
       const int i = c % ext[0];
