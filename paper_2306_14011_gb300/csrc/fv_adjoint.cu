@@ -5,7 +5,7 @@
 // lam^T R = sum over faces f of ds (lam_{f-1} - lam_f) . F_f, F_f the flux
 // between cells f-1 and f from the MUSCL states of cells f-2..f+1.  One CTA
 // per tile computes, for every face whose stencil touches the tile, the
-// cotangents of its left/right states (roe_2F_vjp) and pushes them through the
+// cotangents of its left/right states (roe_F_vjp) and pushes them through the
 // reconstruction to the four stencil cells; each cell then gathers what its
 // faces sent it, so no atomics are needed.  Halos: 3 cells of U, 2 of lam.
 // With transmissive boundaries the faces outside [0, n] do not exist and the
@@ -140,7 +140,7 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
     qL[E] = QL[E];
     qR[E] = QR[E];
     Gb[E] = gb[E];
-    roe_2F_vjp<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gb, bL, bR);
+    roe_F_vjp<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gb, bL, bR);
     double QLb[NV], QRb[NV];
     QLb[0] = bL[0];
     QRb[0] = bR[0];

@@ -2,14 +2,17 @@
 // reconstruction, for the discrete adjoint of the residual (paper Eq. (5) with
 // the fluxes of Eq. (2) and states of Eq. (6)).
 //
-// roe_2F_vjp recomputes the forward quantities of twice the flux of roe_F
-// (fv_device.cuh), in the central form (F(QL) + F(QR)) - sum |lambda| alpha r,
-// and propagates a cotangent Gb of that output (2F) back to its inputs, line
-// by line in reverse.  Conventions at the non-differentiable points follow the
-// forward-mode reference: |x| has derivative sign(x) with sign(+0) = +1, the
-// entropy fix takes the branch the forward pass took, and the limited slope
-// minmod(a, b) passes the derivative of the argument it returned (b on ties)
-// and none when the arguments do not have one strict sign.
+// roe_F_vjp recomputes the forward quantities of roe_F (fv_device.cuh): the
+// upwind physical flux plus the one acoustic wave that crosses from downwind,
+// which equals the central Roe flux (F(QL) + F(QR))/2 - sum |lambda| alpha r/2
+// as a function; it propagates a cotangent Gb of F back to the two states,
+// line by line in reverse.  Conventions at the non-differentiable points
+// follow the forward-mode reference: |x| has derivative sign(x) with
+// sign(+0) = +1 (the upwind side of u~_n = +0 is the left one, where the
+// contact and shear waves drop out, as sign(+0) = +1 gives), the entropy fix
+// takes the branch the forward pass took, and the limited slope minmod(a, b)
+// passes the derivative of the argument it returned (b on ties) and none when
+// the arguments do not have one strict sign.
 #pragma once
 #include "fv_device.cuh"
 
@@ -21,13 +24,11 @@ __device__ __forceinline__ double mul_sign(double x, double s) {
 }
 
 template <int NT>
-__device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
-                                           double efix, double inv2efix, const double (&Gb)[NT + 3],
-                                           double (&QLb)[NT + 3], double (&QRb)[NT + 3]) {
+__device__ __forceinline__ void roe_F_vjp(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
+                                          double efix, double inv2efix, const double (&Gb)[NT + 3],
+                                          double (&QLb)[NT + 3], double (&QRb)[NT + 3]) {
   constexpr int E = NT + 2;
-  // ---------------- forward: 2F in the central form, with the Roe averages
-  // in their two-weight form u~ = wL uL + wR uR, H~ = wL HL + wR HR (the same
-  // function as roe_F, which evaluates it one-sided to save FP64 operations)
+  // ---------------- forward: the quantities of roe_F
   const double tL = rsqrt_fp64(QL[0]);
   const double rL = tL * tL;
   const double sL = QL[0] * tL;
@@ -41,7 +42,6 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   }
   const double pL = g1 * fma(-0.5, kL, QL[E]);
   const double eL = QL[E] + pL;
-  const double HL = eL * rL;
   const double tR = rsqrt_fp64(QR[0]);
   const double rR = tR * tR;
   const double sR = QR[0] * tR;
@@ -55,217 +55,172 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   }
   const double pR = g1 * fma(-0.5, kR, QR[E]);
   const double eR = QR[E] + pR;
-  const double HR = eR * rR;
   const double inv = rcp_fp64(sL + sR);
   const double wL = sL * inv, wR = sR * inv;
-  const double un = fma(wL, unL, wR * unR);
-  double ut[NT];
+  const double dun = unR - unL;
+  const double un = fma(-wL, dun, unR);
+  double ut[NT], dut[NT];
   double q2 = un * un;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    ut[t] = fma(wL, utL[t], wR * utR[t]);
+    dut[t] = utR[t] - utL[t];
+    ut[t] = fma(-wL, dut[t], utR[t]);
     q2 = fma(ut[t], ut[t], q2);
   }
-  const double H = fma(wL, HL, wR * HR);
+  const double Hn = fma(eL, tL, eR * tR);
+  const double H = Hn * inv;
   const double rho = sL * sR;
-  const double hq = half_nonneg(q2);
-  const double c2 = g1 * (H - hq);
+  const double c2 = g1 * (H - half_nonneg(q2));
   const double tc = rsqrt_fp64(c2);
   const double c = c2 * tc;
-  const double ic2 = tc * tc;
+  const bool up_left = __double2hiint(un) >= 0;
+  const double aun = iabs(un);
+  const double sc = isel(up_left, c, ineg(c));
   const double dp = pR - pL;
-  const double dun = unR - unL;
-  const double rc = rho * c;
-  const double rcdun = rc * dun;
-  const double hic2 = half_nonneg(ic2);
-  const double a1 = (dp - rcdun) * hic2;
-  const double a3 = (dp + rcdun) * hic2;
-  const double a2 = fma(-dp, ic2, QR[0] - QL[0]);
-  const double x1 = un - c, x3 = un + c;
-  const double m1 = iabs(x1), m3 = iabs(x3), l2 = iabs(un);
+  const double rsc = rho * sc;
+  const double num = fma(-rsc, dun, dp);
+  const double tc2h = tc * half_nonneg(tc);  // 1 / (2 c~^2)
+  const double alpha = num * tc2h;
+  const double x = aun - c;
+  const bool neg = __double2hiint(x) < 0 && !izero(x);
+  double k = isel(neg, x, 0.0);
   // the fix decision of roe_F (FP32 copies), so both differentiate one function
   const float deltaf = __fmul_rn(f32_trunc(efix), f32_trunc(c));
-  const bool fix1 = f32_trunc(m1) < deltaf, fix3 = f32_trunc(m3) < deltaf;
-  double l1 = m1, l3 = m3, delta = 0.0, s2 = 0.0;
-  const bool anyfix = __any_sync(__activemask(), fix1 || fix3);
+  const bool fix = f32_trunc(iabs(x)) < deltaf;
+  const bool anyfix = __any_sync(__activemask(), fix);
+  double delta = 0.0, s2 = 0.0;
   if (anyfix) {
     delta = efix * c;
-    s2 = tc * inv2efix;
-    const double d2 = delta * delta;
-    l1 = isel(fix1, fma(m1, m1, d2) * s2, m1);
-    l3 = isel(fix3, fma(m3, m3, d2) * s2, m3);
+    s2 = tc * inv2efix;  // 1 / (2 delta)
+    k = isel(fix, fma(-fma(x, x, delta * delta), 0.5 * s2, 0.5 * x), k);
   }
-  const double A1 = l1 * a1, A2 = l2 * a2, A3 = l3 * a3;
-  const double lr = l2 * rho;
-  const double s13 = A1 + A3;
-  const double d13 = A3 - A1;
-  const double cd13 = c * d13;
-  const double D0 = s13 + A2;
-  double B[NT];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) B[t] = lr * (utR[t] - utL[t]);
+  const double g = k * alpha;
+  const double lam = un - sc;
+  const double hr = fma(-c, aun, H);
+  const double m = isel(up_left, QL[1], QR[1]);
+  const double u_n = isel(up_left, unL, unR);
+  const double e = isel(up_left, eL, eR);
 
   // ---------------- reverse
-  double mnLb = Gb[0] + Gb[1] * unL, mnRb = Gb[0] + Gb[1] * unR;
-  double unLb = Gb[1] * QL[1] + Gb[E] * eL, unRb = Gb[1] * QR[1] + Gb[E] * eR;
-  double pLb = Gb[1], pRb = Gb[1];
-  double eLb = Gb[E] * unL, eRb = Gb[E] * unR;
-  double utLb[NT], utRb[NT], utb[NT], Bb[NT];
-  double D0b = -Gb[0];
-  const double Dnb = -Gb[1];
-  const double DEb = -Gb[E];
+  // G0 = m + g; G1 = m u_n + p_up + g lam; G2+t = m ut_up + g ut; GE = u_n e + g hr
+  double mb = fma(Gb[1], u_n, Gb[0]);
+  double u_nb = fma(Gb[E], e, Gb[1] * m);
+  const double pupb = Gb[1];
+  const double eupb = Gb[E] * u_n;
+  double gb = fma(Gb[E], hr, fma(Gb[1], lam, Gb[0]));
+  double utupb[NT], utb[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    mnLb = fma(Gb[2 + t], utL[t], mnLb);
-    mnRb = fma(Gb[2 + t], utR[t], mnRb);
-    utLb[t] = Gb[2 + t] * QL[1];
-    utRb[t] = Gb[2 + t] * QR[1];
-    const double Dtb = -Gb[2 + t];
-    // DE += ut B; Dt = ut D0 + B
-    utb[t] = fma(DEb, B[t], Dtb * D0);
-    Bb[t] = fma(DEb, ut[t], Dtb);
-    D0b = fma(Dtb, ut[t], D0b);
+    mb = fma(Gb[2 + t], isel(up_left, utL[t], utR[t]), mb);
+    utupb[t] = Gb[2 + t] * m;
+    gb = fma(Gb[2 + t], ut[t], gb);
+    utb[t] = Gb[2 + t] * g;
   }
-  // DE = hq A2 + sum ut B + un cd13 + H s13
-  double hqb = DEb * A2;
-  double A2b = DEb * hq;
-  double unb = DEb * cd13;
-  double cd13b = DEb * un;
-  double Hb = DEb * s13;
-  double s13b = DEb * H;
-  // B = lr (utR - utL)
-  double lrb = 0.0;
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    lrb = fma(Bb[t], utR[t] - utL[t], lrb);
-    utRb[t] = fma(Bb[t], lr, utRb[t]);
-    utLb[t] = fma(-Bb[t], lr, utLb[t]);
-  }
-  // Dn = un D0 + cd13
-  unb = fma(Dnb, D0, unb);
-  D0b = fma(Dnb, un, D0b);
-  cd13b += Dnb;
-  // D0 = s13 + A2
-  s13b += D0b;
-  A2b += D0b;
-  // cd13 = c d13; d13 = A3 - A1; s13 = A1 + A3
-  double cb = cd13b * d13;
-  const double d13b = cd13b * c;
-  const double A3b = s13b + d13b, A1b = s13b - d13b;
-  // lr = l2 rho
-  double l2b = lrb * rho;
-  double rhob = lrb * l2;
-  // A_w = l_w a_w
-  const double l1b = A1b * a1, a1b = A1b * l1;
-  l2b = fma(A2b, a2, l2b);
-  const double a2b = A2b * l2;
-  const double l3b = A3b * a3, a3b = A3b * l3;
-  // eigenvalue magnitudes, entropy fix
-  double m1b = l1b, m3b = l3b, deltab = 0.0, tcb = 0.0;
+  const double lamb = Gb[1] * g;
+  const double hrb = Gb[E] * g;
+  // hr = H - c aun ; lam = un - sc
+  double Hb = hrb;
+  double cb = -hrb * aun;
+  double aunb = -hrb * c;
+  double unb = lamb;
+  double scb = -lamb;
+  // g = k alpha
+  const double kb = gb * alpha;
+  const double alphab = gb * k;
+  // k = min(x, 0), or with the fix x/2 - (x^2 + delta^2) / (4 delta)
+  double xb = isel(neg, kb, 0.0);
   if (anyfix) {
-    const double s2b = isel(fix1, l1b * fma(m1, m1, delta * delta), 0.0) +
-                       isel(fix3, l3b * fma(m3, m3, delta * delta), 0.0);
-    m1b = isel(fix1, 2.0 * m1 * s2 * l1b, l1b);
-    m3b = isel(fix3, 2.0 * m3 * s2 * l3b, l3b);
-    deltab = isel(fix1, 2.0 * delta * s2 * l1b, 0.0) + isel(fix3, 2.0 * delta * s2 * l3b, 0.0);
-    tcb = s2b * inv2efix;
+    const double xs = x * s2;  // x / (2 delta)
+    xb = isel(fix, kb * (0.5 - xs), xb);
+    cb = fma(isel(fix, kb * fma(xs, xs, -0.25), 0.0), efix, cb);  // delta = efix c
   }
-  cb = fma(deltab, efix, cb);
-  const double x1b = mul_sign(m1b, x1), x3b = mul_sign(m3b, x3);
-  unb += mul_sign(l2b, un) + x1b + x3b;
-  cb += x3b - x1b;
-  // a2 = drho - dp ic2 ; a1, a3 = (dp -+ rcdun) hic2
-  const double drhob = a2b;
-  double dpb = fma(a1b + a3b, hic2, -a2b * ic2);
-  double ic2b = -a2b * dp;
-  const double rcdunb = (a3b - a1b) * hic2;
-  const double hic2b = fma(a1b, dp - rcdun, a3b * (dp + rcdun));
-  ic2b = fma(0.5, hic2b, ic2b);
-  // rcdun = rc dun ; rc = rho c
-  const double rcb = rcdunb * dun;
-  const double dunb = rcdunb * rc;
-  rhob = fma(rcb, c, rhob);
-  cb = fma(rcb, rho, cb);
-  unRb += dunb;
-  unLb -= dunb;
-  pRb += dpb;
-  pLb -= dpb;
-  // ic2 = tc^2 ; c = c2 tc ; tc = c2^(-1/2)
-  tcb = fma(ic2b, scale_pow2<1>(tc), tcb);
+  // x = aun - c ; aun = |un|
+  aunb += xb;
+  cb -= xb;
+  unb += mul_sign(aunb, un);
+  // alpha = num tc2h ; num = dp - rsc dun ; rsc = rho sc ; tc2h = tc^2 / 2 ; sc = +-c
+  const double numb = alphab * tc2h;
+  double tcb = (alphab * num) * tc;
+  const double dpb = numb;
+  const double rscb = -numb * dun;
+  const double dunb = -numb * rsc;
+  const double rhob = rscb * sc;
+  scb = fma(rscb, rho, scb);
+  cb += isel(up_left, scb, ineg(scb));
+  // c = c2 tc ; tc = c2^(-1/2)
   tcb = fma(cb, c2, tcb);
   double c2b = cb * tc;
-  c2b = fma(tcb, -(scale_pow2<-1>(tc) * ic2), c2b);
-  // c2 = g1 (H - hq)
+  c2b = fma(tcb, -(half_nonneg(tc) * (tc * tc)), c2b);
+  // c2 = g1 (H - q2/2) ; q2 = un^2 + sum ut^2
   Hb = fma(c2b, g1, Hb);
-  hqb = fma(-c2b, g1, hqb);
-  // q2b = hqb / 2 enters as 2 q2b un = hqb un and 2 q2b ut = hqb ut
+  const double q2b2 = -g1 * c2b;  // 2 q2b
+  unb = fma(q2b2, un, unb);
+  // H = Hn inv ; Hn = eL tL + eR tR
+  double invb = Hb * Hn;
+  const double Hnb = Hb * inv;
+  double eLb = Hnb * tL, eRb = Hnb * tR;
+  double tLb = Hnb * eL, tRb = Hnb * eR;
   // rho = sL sR
   double sLb = rhob * sR, sRb = rhob * sL;
-  // H = wL HL + wR HR
-  double wLb = Hb * HL, wRb = Hb * HR;
-  const double HLb = Hb * wL, HRb = Hb * wR;
-  // q2 = un^2 + sum ut^2
-  unb = fma(hqb, un, unb);
+  // ut = utR - wL dut = wL utL + wR utR ; un = unR - wL dun ; dun = unR - unL
+  double wLb = -unb * dun;
+  double utLb[NT], utRb[NT];
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    utb[t] = fma(hqb, ut[t], utb[t]);
-    // ut = wL utL + wR utR
-    wLb = fma(utb[t], utL[t], wLb);
-    wRb = fma(utb[t], utR[t], wRb);
-    utLb[t] = fma(utb[t], wL, utLb[t]);
-    utRb[t] = fma(utb[t], wR, utRb[t]);
+    utb[t] = fma(q2b2, ut[t], utb[t]);
+    wLb = fma(-utb[t], dut[t], wLb);
+    utLb[t] = fma(utb[t], wL, isel(up_left, utupb[t], 0.0));
+    utRb[t] = fma(utb[t], wR, isel(up_left, 0.0, utupb[t]));
   }
-  // un = wL unL + wR unR
-  wLb = fma(unb, unL, wLb);
-  wRb = fma(unb, unR, wRb);
-  unLb = fma(unb, wL, unLb);
-  unRb = fma(unb, wR, unRb);
-  // wL = sL inv ; wR = sR inv ; inv = 1 / (sL + sR)
+  double unLb = fma(unb, wL, isel(up_left, u_nb, 0.0)) - dunb;
+  double unRb = fma(unb, wR, isel(up_left, 0.0, u_nb)) + dunb;
+  // wL = sL inv (wR = 1 - wL) ; inv = 1 / (sL + sR)
   sLb = fma(wLb, inv, sLb);
-  sRb = fma(wRb, inv, sRb);
-  const double invb = fma(wLb, sL, wRb * sR);
+  invb = fma(wLb, sL, invb);
   const double Sb = -invb * inv * inv;
   sLb += Sb;
   sRb += Sb;
+  // dp = pR - pL ; the upwind side's m, p, e
+  double pLb = isel(up_left, pupb - dpb, -dpb), pRb = isel(up_left, dpb, pupb + dpb);
+  eLb += isel(up_left, eupb, 0.0);
+  eRb += isel(up_left, 0.0, eupb);
+  double mnLb = isel(up_left, mb, 0.0), mnRb = isel(up_left, 0.0, mb);
 
-  // left side: HL = eL rL ; eL = E + pL ; pL = g1 (E - kL/2) ; kL = mn unL + sum mt utL
-  double rLb = HLb * eL;
-  eLb = fma(HLb, rL, eLb);
+  // left side: eL = E + pL ; pL = g1 (E - kL/2) ; kL = mn unL + sum mt utL ;
+  // unL = mn rL ; utL = mt rL ; sL = rho tL ; rL = tL^2 ; tL = rho^(-1/2)
   double ELb = eLb;
   pLb += eLb;
   ELb = fma(pLb, g1, ELb);
   const double kLb = -0.5 * g1 * pLb;
   mnLb = fma(kLb, unL, mnLb);
   unLb = fma(kLb, QL[1], unLb);
+  double rLb = 0.0;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     double mtb = kLb * utL[t];
     utLb[t] = fma(kLb, QL[2 + t], utLb[t]);
-    // utL = mt rL
     mtb = fma(utLb[t], rL, mtb);
     rLb = fma(utLb[t], QL[2 + t], rLb);
     QLb[2 + t] = mtb;
   }
-  // unL = mn rL ; sL = rho tL ; rL = tL^2 ; tL = rho^(-1/2)
   mnLb = fma(unLb, rL, mnLb);
   rLb = fma(unLb, QL[1], rLb);
-  double tLb = sLb * QL[0];
+  tLb = fma(sLb, QL[0], tLb);
   double rhoLb = sLb * tL;
   tLb = fma(rLb, scale_pow2<1>(tL), tLb);
-  rhoLb = fma(tLb, -(scale_pow2<-1>(tL) * rL), rhoLb);
-  QLb[0] = rhoLb - drhob;
+  rhoLb = fma(tLb, -(half_nonneg(tL) * rL), rhoLb);
+  QLb[0] = rhoLb;
   QLb[1] = mnLb;
   QLb[E] = ELb;
 
   // right side
-  double rRb = HRb * eR;
-  eRb = fma(HRb, rR, eRb);
   double ERb = eRb;
   pRb += eRb;
   ERb = fma(pRb, g1, ERb);
   const double kRb = -0.5 * g1 * pRb;
   mnRb = fma(kRb, unR, mnRb);
   unRb = fma(kRb, QR[1], unRb);
+  double rRb = 0.0;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     double mtb = kRb * utR[t];
@@ -276,11 +231,11 @@ __device__ __forceinline__ void roe_2F_vjp(const double (&QL)[NT + 3], const dou
   }
   mnRb = fma(unRb, rR, mnRb);
   rRb = fma(unRb, QR[1], rRb);
-  double tRb = sRb * QR[0];
+  tRb = fma(sRb, QR[0], tRb);
   double rhoRb = sRb * tR;
   tRb = fma(rRb, scale_pow2<1>(tR), tRb);
-  rhoRb = fma(tRb, -(scale_pow2<-1>(tR) * rR), rhoRb);
-  QRb[0] = rhoRb + drhob;
+  rhoRb = fma(tRb, -(half_nonneg(tR) * rR), rhoRb);
+  QRb[0] = rhoRb;
   QRb[1] = mnRb;
   QRb[E] = ERb;
 }

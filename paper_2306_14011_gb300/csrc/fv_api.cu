@@ -1030,13 +1030,13 @@ int adjoint(fv_ctx *c, const double *U, const double *lam, double *out, double w
   double h[3];
   for (int d = 0; d < 3; ++d) h[d] = (d < g.dim) ? g.len[d] / g.n[d] : 1.0;
   for (int d = 0; d < 3; ++d) {
-    if (w_dt == 0.0) {  // residual: face area / 2 (roe_2F_vjp differentiates 2F)
+    if (w_dt == 0.0) {  // residual: the face area
       double ds = 1.0;
       for (int e = 0; e < g.dim; ++e)
         if (e != d) ds *= h[e];
-      a.scale[d] = 0.5 * ds;
-    } else {  // RK stage: -w dt / (2 dx_d), the transposed stage update
-      a.scale[d] = -w_dt * 0.5 / h[d];
+      a.scale[d] = ds;
+    } else {  // RK stage: -w dt / dx_d, the transposed stage update
+      a.scale[d] = -w_dt / h[d];
     }
   }
   a.g1 = c->scheme.gamma - 1.0;
