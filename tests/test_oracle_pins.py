@@ -153,6 +153,50 @@ def test_roe_flux_equals_half_sum_minus_abs_roe_matrix_jump(dim):
             np.testing.assert_allclose(F, Fref, rtol=1e-11, atol=1e-11 * np.abs(Fref).max())
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("efix", [0.0, 0.1, 0.6])
+def test_roe_flux_is_the_upwind_flux_plus_one_acoustic_wave(dim, efix):
+    """The reading the GPU kernels evaluate: by Roe's property the central
+    flux equals F(Q_up) + k alpha_s r_s taken from the upwind side of the
+    Roe-averaged normal velocity u~_n, with x = |u~_n| - c~, k = (x - |x|*)/2
+    (|x|* Harten's fixed magnitude, efix < 1), alpha_s = dp/(2c~^2) -+
+    rho~ du_n/(2c~), r_s = (1, u~_n -+ c~, u~_t, H~ - c~|u~_n|) (upper signs
+    for u~_n >= 0).  Restated here in numpy from the Roe averages, against the
+    oracle's central-form flux, for subsonic, sonic and supersonic pairs of
+    both signs of u~_n; beyond the fix band supersonic faces carry the
+    upwind physical flux alone."""
+    rng = np.random.default_rng(10 * dim + int(10 * efix))
+    s = O.scheme(efix=efix)
+    g1 = G - 1
+    for trial in range(60):
+        ql = _state(rng.uniform(0.2, 2), rng.uniform(-2.5, 2.5, dim), rng.uniform(0.2, 2))
+        qr = _state(rng.uniform(0.2, 2), rng.uniform(-2.5, 2.5, dim), rng.uniform(0.2, 2))
+        for d in range(dim):
+            rl, rr = ql[0], qr[0]
+            ul, ur = ql[1:1 + dim] / rl, qr[1:1 + dim] / rr
+            pl = g1 * (ql[-1] - 0.5 * rl * ul @ ul)
+            pr = g1 * (qr[-1] - 0.5 * rr * ur @ ur)
+            Hl, Hr = (ql[-1] + pl) / rl, (qr[-1] + pr) / rr
+            wl, wr = np.sqrt(rl), np.sqrt(rr)
+            u = (wl * ul + wr * ur) / (wl + wr)
+            H = (wl * Hl + wr * Hr) / (wl + wr)
+            rho = wl * wr
+            c = np.sqrt(g1 * (H - 0.5 * u @ u))
+            un = u[d]
+            sg = 1.0 if un >= 0 else -1.0
+            x = abs(un) - c
+            delta = efix * c
+            k = (x - (x * x + delta * delta) / (2 * delta)) / 2 if abs(x) < delta else min(x, 0.0)
+            alpha = (pr - pl) / (2 * c * c) - sg * rho * (ur[d] - ul[d]) / (2 * c)
+            r = np.concatenate([[1.0], u, [H - c * abs(un)]])
+            r[1 + d] = un - sg * c
+            F = O.physical_flux(ql if sg > 0 else qr, d) + k * alpha * r
+            Fo = O.roe_flux(ql, qr, d, dim, s)
+            np.testing.assert_allclose(F, Fo, rtol=1e-12, atol=1e-12 * np.abs(Fo).max())
+            if x >= delta and x > 0:  # supersonic beyond the fix band: the upwind physical flux
+                np.testing.assert_allclose(Fo, O.physical_flux(ql if sg > 0 else qr, d), rtol=1e-14, atol=1e-14)
+
+
 def test_roe_flux_of_equal_states_is_the_physical_flux_bitwise():
     rng = np.random.default_rng(1)
     for dim in (2, 3):
