@@ -328,9 +328,10 @@ typedef struct fv_tune_report {
  * retrained on everything measured so far (the held-out 25% of the random
  * sample excepted); then refine the best measured configuration by
  * coordinate descent (each parameter in turn over its value set).  With
- * opts->exhaustive a judge is timed over a reduced space: FV_FUSED, every
- * configuration with one shared (tile, threads) for the three stages, box
- * tiles, TMA loads and the default time-step kernel; FV_SPLIT, one shared
+ * opts->exhaustive an exhaustive search of a reduced space is timed:
+ * FV_FUSED, every configuration with one shared (tile, threads) for the
+ * three stages, box tiles, TMA loads and the default time-step kernel;
+ * FV_SPLIT, one shared
  * (gang, vector) for every kernel (120 points).  Finally the search's best,
  * the default and (if run) the exhaustive best are timed interleaved
  * opts->final_repeats times; the fastest by median is returned in *best and

@@ -303,7 +303,7 @@ void pad(const Grid &g, const Layout &L, const T *U, std::vector<T> &P) {
 // Each face flux is evaluated once, stored, and read by both cells that share it.
 // TERMS = true instead accumulates the magnitudes of the terms that sum:
 // sum_d ds_d (|F_{k+1/2,d}| + |F_{k-1/2,d}|) + |Omega| |S_k| (the scale of
-// the residual's rounding error, used to judge residuals that vanish).
+// the residual's rounding error, the tolerance floor for residuals that vanish).
 template <class T, bool TERMS = false>
 void residual(const Grid &g, const Scheme &s, const T *U, T *R, const double *S = nullptr) {
   Layout L(g);

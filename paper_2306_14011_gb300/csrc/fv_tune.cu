@@ -446,7 +446,7 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
   }
   fv_launch tuned = to_launch(sp, cfgs[best_i], sms, deflt);
 
-  // ---- 4. exhaustive judge on the reduced space (shared tile and threads)
+  // ---- 4. exhaustive search of the reduced space (shared tile and threads)
   fv_launch exh_best;
   memset(&exh_best, 0, sizeof(exh_best));
   int n_exh = 0;

@@ -209,7 +209,7 @@ def test_split_mode_rejections():
 
 def test_tuner_searches_the_papers_space():
     """The tuner on the split kernels: the paper's 14 parameters and 10^7 x
-    12^7 points; the judge times 120 shared (gang, vector) pairs; the
+    12^7 points; the exhaustive search times 120 shared (gang, vector) pairs; the
     returned launch is a valid split launch no slower than the default."""
     g, U = I.kelvin_helmholtz(256, seed=1)
     with fv.Solver(g, mode=fv.FV_SPLIT) as s:

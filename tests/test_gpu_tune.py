@@ -1,6 +1,6 @@
 """GPU tests of the autotuner (paper Sec. 3.3-3.6): the surrogate network's
 kernels against the NumPy oracle, and fv_tune against the default launch and
-the exhaustive judge on the reduced space."""
+the exhaustive search of the reduced space."""
 import json
 import os
 
@@ -63,7 +63,7 @@ def test_mlp_training_matches_numpy_oracle(sizes, epochs, stop):
     np.testing.assert_allclose(out.cpu().numpy(), M.predict(got, X), rtol=1e-13, atol=1e-13)
 
 
-def test_tuner_beats_default_and_matches_exhaustive_judge():
+def test_tuner_beats_default_and_matches_exhaustive_search():
     g, U = I.kelvin_helmholtz(1024, seed=1)
     Ud = torch.from_numpy(U).cuda()
     with fv.Solver(g) as s:
@@ -85,7 +85,7 @@ def test_tuner_beats_default_and_matches_exhaustive_judge():
         # the surrogate predicts held-out configurations better than their mean does
         assert rep["r2_test"] > 0.0
         # the returned launch is the fastest of the search's pick, the default and
-        # the exhaustive judge; the search alone (which starts from the default)
+        # the exhaustive search; the search alone (which starts from the default)
         # is within 3% timing noise of both
         assert rep["t_tuned"] <= min(rep["t_default"], rep["t_search"])
         assert rep["chosen"] in (0, 1, 2)

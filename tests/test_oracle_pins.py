@@ -31,7 +31,7 @@ def test_free_stream_residual_is_exactly_zero(dim, bc):
 
 @pytest.mark.parametrize("dim", [2, 3])
 def test_residual_term_magnitudes_of_a_uniform_state(dim):
-    """residual_terms (the scale the GPU parity tests judge vanishing
+    """residual_terms (the scale the GPU parity tests measure vanishing
     residuals against): for a uniform state every face flux is the Euler flux
     F_d(Q), so each cell's sum is sum_d 2 |F_d(Q)| ds_d, plus |Omega| |S|."""
     g = I.grid2d(6, 5, 1.0, 2.0) if dim == 2 else I.grid3d(5, 4, 6, 1.0, 2.0, 3.0)
