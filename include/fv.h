@@ -331,9 +331,9 @@ typedef struct fv_tune_report {
  * opts->exhaustive an exhaustive search of a reduced space is timed:
  * FV_FUSED, every configuration with one shared (tile, threads) for the
  * three stages, box tiles, TMA loads and the default time-step kernel;
- * FV_SPLIT, one shared
- * (gang, vector) for every kernel (120 points).  Finally the search's best,
- * the default and (if run) the exhaustive best are timed interleaved
+ * FV_SPLIT, one shared (gang, vector) for every kernel (120 points).
+ * Finally the search's best, the default and (if run) the exhaustive best
+ * are timed interleaved
  * opts->final_repeats times; the fastest by median is returned in *best and
  * installed in ctx.  rep may be NULL.  Waits for completion. */
 int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *best, fv_tune_report *rep);
