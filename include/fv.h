@@ -333,9 +333,9 @@ typedef struct fv_tune_report {
  * three stages, box tiles, TMA loads and the default time-step kernel;
  * FV_SPLIT, one shared (gang, vector) for every kernel (120 points).
  * Finally the search's best, the default and (if run) the exhaustive best
- * are timed interleaved
- * opts->final_repeats times; the fastest by median is returned in *best and
- * installed in ctx.  rep may be NULL.  Waits for completion. */
+ * are timed interleaved opts->final_repeats times; the fastest by median is
+ * returned in *best and installed in ctx.  rep may be NULL.  Waits for
+ * completion. */
 int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *best, fv_tune_report *rep);
 
 /* The autotuner's search space for a dim-dimensional grid in kernel
