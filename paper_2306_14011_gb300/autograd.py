@@ -8,6 +8,11 @@ state every `every` steps; the backward pass re-runs each segment from its
 checkpoint, keeping that segment's step states, then reverses it.  Forward
 work is about doubled; stored states are nsteps/every + every.
 
+FvRevolveFunction.apply(U0, solver, nsteps, dt, snapshots) differentiates the
+same run with at most `snapshots` stored states besides U0, placed by the
+optimal offline (binomial) checkpointing schedule of Griewank's revolve: the
+fewest recomputed steps for that memory (revolve_table).
+
 FvResidualFunction.apply(U, solver) is R_h(U) (Eq. (5)) with its VJP, and
 FvStepFunction.apply(U, solver, dt) one SSP-RK3 step with the step held at dt
 (Eq. (4)) with its VJP, for composing steps with other torch operations.
@@ -15,6 +20,9 @@ Everything runs in the library's kernels; torch only holds the tensors.
 """
 from __future__ import annotations
 
+import functools
+
+import numpy as np
 import torch
 
 from . import fv
@@ -85,6 +93,102 @@ class FvRunFunction(torch.autograd.Function):
                 fv.fv_adjoint_vjp(solver.ctx, fv.FV_VJP_RKSTEP, states[s], lam, dt, out)
                 lam, out = out, lam
         ctx.ckpts = None
+        return lam, None, None, None, None
+
+
+@functools.lru_cache(maxsize=16)
+def revolve_table(nsteps: int, snapshots: int):
+    """Optimal offline checkpointing of `nsteps` steps reversed from a stored
+    start state with `snapshots` further states (binomial checkpointing,
+    Griewank 1992; Griewank and Walther's revolve).  Returns (cost, split),
+    int64 arrays of shape (snapshots + 1, nsteps + 1): cost[c][l] is the
+    fewest forward steps that reverse l steps with c free snapshots, split[c][l]
+    the steps to advance before storing the next state:
+        cost[c][l] = min over 0 < m < l of  m + cost[c-1][l-m] + cost[c][m],
+        cost[c][1] = 0,  cost[0][l] = l (l - 1) / 2  (recompute every step)."""
+    n, C = int(nsteps), int(snapshots)
+    if n < 1 or C < 0:
+        raise ValueError("need nsteps >= 1 and snapshots >= 0")
+    ls = np.arange(n + 1, dtype=np.int64)
+    cost = np.zeros((C + 1, n + 1), dtype=np.int64)
+    split = np.zeros((C + 1, n + 1), dtype=np.int64)
+    cost[0] = np.maximum(ls * (ls - 1) // 2, 0)
+    for c in range(1, C + 1):
+        for l in range(2, n + 1):
+            m = ls[1:l]
+            tot = m + cost[c - 1][l - m] + cost[c][m]
+            j = int(np.argmin(tot))
+            cost[c][l] = tot[j]
+            split[c][l] = m[j]
+    cost.setflags(write=False)
+    split.setflags(write=False)
+    return cost, split
+
+
+def _reverse(solver, dt, start, a, b, free, split, lam, out):
+    """Reverse steps a..b-1 given the state at step a (`start`, unchanged):
+    on entry lam is the cotangent of the state at b, on return the first of
+    the returned pair is that of the state at a (the second is scratch)."""
+    while b > a:
+        if b - a == 1:
+            solver.rk_step_vjp(start, lam, dt, out)
+            return out, lam
+        if free == 0:  # no snapshot left: recompute each step from `start`
+            X = torch.empty_like(start)
+            for j in range(b - 1, a - 1, -1):
+                X.copy_(start)
+                for _ in range(j - a):
+                    solver.rk_step(X, dt)
+                solver.rk_step_vjp(X, lam, dt, out)
+                lam, out = out, lam
+            return lam, out
+        m = int(split[free][b - a])
+        S = start.clone()
+        for _ in range(m):
+            solver.rk_step(S, dt)
+        lam, out = _reverse(solver, dt, S, a + m, b, free - 1, split, lam, out)
+        del S
+        b = a + m  # the left part keeps the same number of free snapshots
+    return lam, out
+
+
+class FvRevolveFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U0, solver, nsteps: int, dt: float, snapshots: int = 20):
+        if not dt > 0.0:
+            raise ValueError("differentiated runs need a fixed step dt > 0")
+        nsteps, snapshots = int(nsteps), int(snapshots)
+        _, split = revolve_table(max(1, nsteps), snapshots)
+        U = U0.detach().contiguous().clone()
+        # the schedule's first advances: from step 0, store a state after
+        # split[c][remaining] steps, c = snapshots, snapshots - 1, ...
+        pos, states = [0], [U0.detach().contiguous()]
+        free = snapshots
+        while free > 0 and nsteps - pos[-1] > 1:
+            m = int(split[free][nsteps - pos[-1]])
+            solver.run(U, m, dt_fixed=dt)
+            pos.append(pos[-1] + m)
+            states.append(U.clone())
+            free -= 1
+        solver.run(U, nsteps - pos[-1], dt_fixed=dt)
+        ctx.solver, ctx.nsteps, ctx.dt, ctx.snapshots = solver, nsteps, dt, snapshots
+        ctx.pos, ctx.states = pos, states
+        return U
+
+    @staticmethod
+    def backward(ctx, gU):
+        solver, dt, n, C = ctx.solver, ctx.dt, ctx.nsteps, ctx.snapshots
+        _, split = revolve_table(max(1, n), C)
+        pos, states = ctx.pos, ctx.states
+        lam = gU.contiguous().clone()
+        out = torch.empty_like(lam)
+        k = len(pos) - 1
+        if n > 0:
+            lam, out = _reverse(solver, dt, states[k], pos[k], n, C - k, split, lam, out)
+        for i in range(k - 1, -1, -1):
+            states[i + 1] = None  # its snapshot is free again
+            lam, out = _reverse(solver, dt, states[i], pos[i], pos[i + 1], C - i, split, lam, out)
+        ctx.states = None
         return lam, None, None, None, None
 
 

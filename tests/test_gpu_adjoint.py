@@ -331,3 +331,22 @@ def test_config5_minmod_gradient_is_independent_of_checkpointing_and_matches_dua
     print("minmod 256^2 x 400: adjoint %.12e, dual on the GPU trajectory %.12e (rel %.2e), on the oracle's %.12e "
           "(rel %.2e), growth %.3e" % (ad, exact, abs(ad - exact) / abs(exact), own, abs(ad - own) / abs(own), growth))
     assert abs(ad - exact) <= 1e-5 * abs(exact), (ad, exact, own, growth)
+
+
+def test_revolve_checkpointing_gives_the_same_gradient():
+    """FvRevolveFunction (binomial checkpointing with 0, 4 or 60 stored
+    states for 50 steps) reverses through the same step states as two-level
+    checkpointing: the gradients are bitwise equal."""
+    from paper_2306_14011_gb300.autograd import FvRevolveFunction, FvRunFunction, kinetic_energy
+    g, U = I.isentropic_vortex(128, seed=1)
+    with fv.Solver(g) as s:
+        Ud = dev(U)
+        dt = s.time_step(Ud)
+        grads = []
+        for fn, arg in ((FvRunFunction, 20), (FvRevolveFunction, 4), (FvRevolveFunction, 0),
+                        (FvRevolveFunction, 60)):
+            U0 = Ud.clone().requires_grad_()
+            kinetic_energy(fn.apply(U0, s, 50, dt, arg), g).backward()
+            grads.append(U0.grad.clone())
+    for gr in grads[1:]:
+        assert torch.equal(gr, grads[0])
