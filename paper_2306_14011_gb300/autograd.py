@@ -162,7 +162,7 @@ class FvRevolveFunction(torch.autograd.Function):
         U = U0.detach().contiguous().clone()
         # the schedule's first advances: from step 0, store a state after
         # split[c][remaining] steps, c = snapshots, snapshots - 1, ...
-        pos, states = [0], [U0.detach().contiguous()]
+        pos, states = [0], [U0.detach().contiguous().clone()]  # a copy: U0 may change before backward
         free = snapshots
         while free > 0 and nsteps - pos[-1] > 1:
             m = int(split[free][nsteps - pos[-1]])
