@@ -45,7 +45,7 @@ typedef enum fv_status {
   FV_ECUDA = 3,          /* a CUDA runtime or driver call failed */
   FV_ENONPHYSICAL = 4,   /* a cell had rho <= 0, p <= 0 or a NaN */
   FV_ETIMEOUT = 5,       /* a bounded device-side wait gave up */
-  FV_EUNSUPPORTED = 6    /* valid request this build does not implement */
+  FV_EUNSUPPORTED = 6    /* valid request the library does not support */
 } fv_status;
 
 enum { FV_BC_PERIODIC = 0, FV_BC_TRANSMISSIVE = 1 };

@@ -643,7 +643,7 @@ const char *fv_strerror(int status) {
     case FV_ECUDA: return "CUDA error";
     case FV_ENONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN)";
     case FV_ETIMEOUT: return "device-side wait timed out";
-    case FV_EUNSUPPORTED: return "unsupported by this build";
+    case FV_EUNSUPPORTED: return "valid request the library does not support";
     default: return "unknown status";
   }
 }
