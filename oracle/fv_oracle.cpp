@@ -121,55 +121,30 @@ double orc_run(const Grid *g, const Scheme *s, double *U, int nsteps, double dt_
 
 }  // extern "C"
 
-// Residual of a list of cells only (flat interior indices k*ny*nx + j*nx + i),
-// for sampled checks on grids too large for the full oracle.  out: [ncells][nv].
-template <class T>
-void residual_cells(const Grid *g, const Scheme *s, const double *U, long ncells, const long *cells, double *out) {
-  Layout L(*g);
-  const int nv = L.nv;
-#pragma omp parallel for schedule(dynamic, 64)
-  for (long c = 0; c < ncells; ++c) {
-    long id = cells[c];
-    int i = (int)(id % L.n[0]), j = (int)((id / L.n[0]) % L.n[1]), k = (int)(id / ((long)L.n[0] * L.n[1]));
-    T R[5] = {T(0), T(0), T(0), T(0), T(0)};
-    for (int d = 0; d < L.dim; ++d) {
-      double ds = 1.0;
-      for (int a = 0; a < L.dim; ++a)
-        if (a != d) ds *= L.h[a];
-      T Fside[2][5];
-      for (int side = 0; side < 2; ++side) {  // face k-1/2 then k+1/2
-        T QL[5], QR[5];
-        for (int v = 0; v < nv; ++v) {
-          T q[4];
-          for (int t = 0; t < 4; ++t) {
-            int c3[3] = {i, j, k};
-            c3[d] += side + t - 2;  // cells k-2+side .. k+1+side
-            int si = ghost_source(c3[0], L.n[0], g->bc[0]);
-            int sj = ghost_source(c3[1], L.n[1], g->bc[1]);
-            int sk = (L.dim == 3) ? ghost_source(c3[2], L.n[2], g->bc[2]) : 0;
-            q[t] = U[L.idx(v, si, sj, sk)];
-          }
-          muscl(*s, q[0], q[1], q[2], q[3], QL[v], QR[v]);
-        }
-        roe_flux(*s, L.dim, d, QL, QR, Fside[side]);
-      }
-      for (int v = 0; v < nv; ++v) R[v] += (Fside[1][v] - Fside[0][v]) * ds;
-    }
-    for (int v = 0; v < nv; ++v) out[c * nv + v] = (double)R[v];
-  }
-}
-
 extern "C" {
 
-int orc_residual_cells(const Grid *g, const Scheme *s, const double *U, long ncells, const long *cells, double *out) {
-  residual_cells<double>(g, s, U, ncells, cells, out);
+// The residual of Eq. (5) at the listed cells (flat interior indices), equal
+// to the matching entries of orc_residual.  S: the source of the whole grid,
+// or NULL.  out: [ncells][nv].  Returns 0, or -1 for an index outside the grid.
+static bool cells_in_grid(const Grid *g, long ncells, const long *cells) {
+  Layout L(*g);
+  for (long c = 0; c < ncells; ++c)
+    if (cells[c] < 0 || cells[c] >= (long)L.cells()) return false;
+  return true;
+}
+
+int orc_residual_cells(const Grid *g, const Scheme *s, const double *U, long ncells, const long *cells, double *out,
+                       const double *S) {
+  if (!cells_in_grid(g, ncells, cells)) return -1;
+  residual_cells<double>(*g, *s, U, ncells, cells, out, S);
   return 0;
 }
 
 // The same in extended precision (long double), rounded to double at the end.
 int orc_residual_cells_ext(const Grid *g, const Scheme *s, const double *U, long ncells, const long *cells,
-                           double *out) {
-  residual_cells<long double>(g, s, U, ncells, cells, out);
+                           double *out, const double *S) {
+  if (!cells_in_grid(g, ncells, cells)) return -1;
+  residual_cells<long double>(*g, *s, U, ncells, cells, out, S);
   return 0;
 }
 

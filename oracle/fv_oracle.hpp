@@ -294,6 +294,27 @@ void pad(const Grid &g, const Layout &L, const T *U, std::vector<T> &P) {
         }
 }
 
+// Flux across the face between Q_k and Q_{k+1} normal to axis d, from the
+// four-cell stencil q = (Q_{k-1}, Q_k, Q_{k+1}, Q_{k+2}) along that axis:
+// the MUSCL face states of Eq. (6), applied to each conserved component
+// (Sec. 3.1) or, with RECON_PRIMITIVE, to (rho, u, p) and converted back to
+// conserved variables, then the Roe flux between them.
+template <class T>
+void stencil_flux(const Scheme &s, int dim, int d, const T (&q)[4][5], T *F) {
+  const int nv = dim + 2;
+  T QL[5], QR[5];
+  if (s.recon == RECON_PRIMITIVE) {
+    T w[4][5], WL[5], WR[5];
+    for (int m = 0; m < 4; ++m) to_primitive(s, dim, q[m], w[m]);
+    for (int v = 0; v < nv; ++v) muscl(s, w[0][v], w[1][v], w[2][v], w[3][v], WL[v], WR[v]);
+    to_conserved(s, dim, WL, QL);
+    to_conserved(s, dim, WR, QR);
+  } else {
+    for (int v = 0; v < nv; ++v) muscl(s, q[0][v], q[1][v], q[2][v], q[3][v], QL[v], QR[v]);
+  }
+  roe_flux(s, dim, d, QL, QR, F);
+}
+
 // Spatial residual of Eq. (5): for every cell,
 //   R_k = sum over its faces of F.n ds - |Omega| S_k
 //       = sum_d ds_d (F_{k+1/2,d} - F_{k-1/2,d}) - |Omega| S_k,
@@ -328,26 +349,14 @@ void residual(const Grid &g, const Scheme &s, const T *U, T *R, const double *S 
       int i = (int)(f % fn[0]), j = (int)((f / fn[0]) % fn[1]), k = (int)(f / ((long)fn[0] * fn[1]));
       // the cells left of the face: (i,j,k) - e_d
       int a = i - e[0], b = j - e[1], c = k - e[2];
-      T QL[5], QR[5], Ff[5];
-      T q[4][5];  // the stencil Q_{k-1}, Q_k, Q_{k+1}, Q_{k+2}
+      T q[4][5], Ff[5];  // the stencil Q_{k-1}, Q_k, Q_{k+1}, Q_{k+2}
       for (int v = 0; v < nv; ++v) {
         q[0][v] = P[L.pidx(v, a - e[0], b - e[1], c - e[2])];
         q[1][v] = P[L.pidx(v, a, b, c)];
         q[2][v] = P[L.pidx(v, i, j, k)];
         q[3][v] = P[L.pidx(v, i + e[0], j + e[1], k + e[2])];
       }
-      if (s.recon == RECON_PRIMITIVE) {
-        // Eq. (6) applied to the primitive variables, the face states then
-        // converted back to conserved variables for the flux
-        T w[4][5], WL[5], WR[5];
-        for (int m = 0; m < 4; ++m) to_primitive(s, L.dim, q[m], w[m]);
-        for (int v = 0; v < nv; ++v) muscl(s, w[0][v], w[1][v], w[2][v], w[3][v], WL[v], WR[v]);
-        to_conserved(s, L.dim, WL, QL);
-        to_conserved(s, L.dim, WR, QR);
-      } else {
-        for (int v = 0; v < nv; ++v) muscl(s, q[0][v], q[1][v], q[2][v], q[3][v], QL[v], QR[v]);
-      }
-      roe_flux(s, L.dim, d, QL, QR, Ff);
+      stencil_flux(s, L.dim, d, q, Ff);
       for (int v = 0; v < nv; ++v) F[(size_t)v * nface + f] = Ff[v];
     }
 #pragma omp parallel for schedule(static)
@@ -373,6 +382,53 @@ void residual(const Grid &g, const Scheme &s, const T *U, T *R, const double *S 
       else
         R[c] = R[c] - vol * T(S[c]);
     }
+  }
+}
+
+// The residual of Eq. (5) at a list of cells only (flat interior indices
+// k*ny*nx + j*nx + i), for sampled checks on grids too large for the full
+// residual.  Per cell and axis it evaluates the two faces k-1/2 and k+1/2
+// from their stencils, each cell of which is read through the boundary map
+// (no ghost-padded copy of the grid), and sums the differences in the order
+// `residual` does, so both give the same doubles.  S: the cell-averaged
+// source of the whole grid (layout of U) or NULL.  out: [ncells][nv].
+template <class T>
+void residual_cells(const Grid &g, const Scheme &s, const double *U, long ncells, const long *cells, double *out,
+                    const double *S = nullptr) {
+  Layout L(g);
+  const int nv = L.nv;
+  double vol = 1.0;
+  for (int a = 0; a < L.dim; ++a) vol *= L.h[a];
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long c = 0; c < ncells; ++c) {
+    const long id = cells[c];
+    const int i = (int)(id % L.n[0]), j = (int)((id / L.n[0]) % L.n[1]);
+    const int k = (int)(id / ((long)L.n[0] * L.n[1]));
+    T R[5] = {T(0.0), T(0.0), T(0.0), T(0.0), T(0.0)};
+    for (int d = 0; d < L.dim; ++d) {
+      double ds = 1.0;
+      for (int a = 0; a < L.dim; ++a)
+        if (a != d) ds *= L.h[a];
+      T Fside[2][5];
+      for (int side = 0; side < 2; ++side) {  // side 0: face k-1/2, side 1: face k+1/2
+        // the face between cells k-1+side and k+side has the stencil
+        // k-2+side .. k+1+side along axis d
+        T q[4][5];
+        for (int t = 0; t < 4; ++t) {
+          int c3[3] = {i, j, k};
+          c3[d] += side + t - 2;
+          const int si = ghost_source(c3[0], L.n[0], g.bc[0]);
+          const int sj = ghost_source(c3[1], L.n[1], g.bc[1]);
+          const int sk = (L.dim == 3) ? ghost_source(c3[2], L.n[2], g.bc[2]) : 0;
+          for (int v = 0; v < nv; ++v) q[t][v] = T(U[L.idx(v, si, sj, sk)]);
+        }
+        stencil_flux(s, L.dim, d, q, Fside[side]);
+      }
+      for (int v = 0; v < nv; ++v) R[v] += (Fside[1][v] - Fside[0][v]) * ds;
+    }
+    if (S)
+      for (int v = 0; v < nv; ++v) R[v] = R[v] - vol * T(S[(size_t)v * L.cells() + (size_t)id]);
+    for (int v = 0; v < nv; ++v) out[c * nv + v] = value(R[v]);
   }
 }
 

@@ -62,8 +62,8 @@ def load_library(path: str):
         L.orc_run.restype = C.c_double
         L.orc_residual_ext.argtypes = [GP, SP, _D, _D, _D]
         L.orc_residual_terms.argtypes = [GP, SP, _D, _D, _D]
-        L.orc_residual_cells.argtypes = [GP, SP, _D, C.c_long, _L, _D]
-        L.orc_residual_cells_ext.argtypes = [GP, SP, _D, C.c_long, _L, _D]
+        L.orc_residual_cells.argtypes = [GP, SP, _D, C.c_long, _L, _D, _D]
+        L.orc_residual_cells_ext.argtypes = [GP, SP, _D, C.c_long, _L, _D, _D]
         L.orc_roe_flux.argtypes = [SP, C.c_int, C.c_int, _D, _D, _D]
         L.orc_roe_flux.restype = None
         L.orc_physical_flux.argtypes = [SP, C.c_int, C.c_int, _D, _D]
@@ -130,14 +130,20 @@ def residual_terms(g, U, s: Scheme | None = None, S=None) -> np.ndarray:
     return R
 
 
-def residual_cells(g, U, cells, s: Scheme | None = None, extended: bool = False) -> np.ndarray:
-    """Residual of the listed cells (flat interior indices); shape (len(cells), nvar).
-    extended=True evaluates in long double and rounds the result to double."""
+def residual_cells(g, U, cells, s: Scheme | None = None, extended: bool = False, S=None) -> np.ndarray:
+    """R_h of Eq. (5) at the listed cells (flat interior indices), the same
+    values as residual() there; shape (len(cells), nvar).  S: the source of the
+    whole grid (None: 0).  extended=True evaluates in long double and rounds
+    the result to double."""
     U = _check(g, U)
+    S = None if S is None else _check(g, S)
     cells = np.ascontiguousarray(cells, dtype=np.int64)
     out = np.empty((cells.size, g.nvar), dtype=np.float64)
     fn = lib().orc_residual_cells_ext if extended else lib().orc_residual_cells
-    fn(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), cells.size, cells.ctypes.data_as(_L), _ptr(out))
+    rc = fn(C.byref(grid(g)), C.byref(s or scheme()), _ptr(U), cells.size, cells.ctypes.data_as(_L), _ptr(out),
+            None if S is None else _ptr(S))
+    if rc != 0:
+        raise ValueError("residual_cells: a cell index lies outside the grid")
     return out
 
 

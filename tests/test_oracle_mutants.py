@@ -37,10 +37,16 @@ MUTANTS = [
     ("RK stage 2 weights", "U2[c] = 0.75 * U[c] + 0.25 * (", "U2[c] = 0.5 * U[c] + 0.5 * ("),
     ("RK stage 3 weights", "U[c] = (1.0 / 3.0) * U[c] + (2.0 / 3.0) * (", "U[c] = 0.5 * U[c] + 0.5 * ("),
     ("CFL wave speed", "sum = sum + (fabs(u[a]) + c) / L.h[a];", "sum = sum + (fabs(u[a]) - c) / L.h[a];"),
+    ("sampled residual: stencil shifted by one cell", "c3[d] += side + t - 2;", "c3[d] += side + t - 1;"),
+    ("sampled residual: boundary of the wrong axis", "const int sj = ghost_source(c3[1], L.n[1], g.bc[1]);",
+     "const int sj = ghost_source(c3[1], L.n[1], g.bc[0]);"),
+    ("sampled residual: source sign", "R[v] = R[v] - vol * T(S[(size_t)v * L.cells() + (size_t)id]);",
+     "R[v] = R[v] + vol * T(S[(size_t)v * L.cells() + (size_t)id]);"),
 ]
 
 
 def _pin_checks():
+    import test_oracle_cells as C
     import test_oracle_pins as P
     return [
         lambda: P.test_free_stream_residual_is_exactly_zero(2, 0),
@@ -62,6 +68,8 @@ def _pin_checks():
         P.test_time_step_of_uniform_flow_closed_form,
         P.test_ssp_rk3_is_third_order_in_time,
         lambda: P.test_sod_tube_converges_to_exact_solution(0),
+        lambda: C.test_residual_cells_equal_the_full_residual_bitwise("2d_6x5_mixed", "minmod", True),
+        lambda: C.test_residual_cells_equal_the_full_residual_bitwise("3d_5x6x7_mixed", "primitive", False),
     ]
 
 
