@@ -10,6 +10,19 @@ keeps evolving across steps as in the 200-step run.
           the state in, advances it and copies it back.
 The state (537 MB) is larger than L2 (129 MB), so no flush is needed.
 
+At one GPU the default run adds two objects to the line:
+  tuned     -- the autotuner (FCNN surrogate, Sec. 3.3-3.6) on KH 4096^2 with a
+               bounded sample, then the naive default launch (32x8 threads,
+               one cell per thread, a grid covering the domain), the library's
+               default launch, the search's pick and the exhaustive best of the
+               reduced space, timed interleaved (median of >= 5 replays each);
+  workloads -- short timed runs of the other forward configurations (3D
+               Taylor-Green 384^3, the 96-grid batched Sod set) and of the
+               adjoint gradient (1024^2 vortex, 400 steps), each with its own
+               clocks and CPU-oracle baseline.
+--launch TILE:THREADS[:march] times one explicit launch (all three RK stages)
+instead of the default.
+
 --impl reference times the CPU oracle (the only reference this paper has; it
 ships no code) on the host cores, on a bounded band of the same workload.
 Multi-GPU: the method does not shard here; N ranks run N independent replicas
@@ -58,6 +71,37 @@ STAGE_TRAFFIC = {"bytes": 1.3894e9, "source_hash": "b4695b9080b1984a", "tile": [
 # sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on, mean of the three
 # stages at 2048^2 / 192^3), for the kernel sources with this hash.
 STAGE_FP64_INST = {"2d": 190.9, "3d": 361.8, "source_hash": "b4695b9080b1984a"}
+
+
+# The naive default launch of the tuning comparison: 32x8 threads, one cell
+# per thread, one CTA per 32x8 tile covering the domain (the analogue of a
+# directive compiler's default launch).
+NAIVE_TILE_2D, NAIVE_THREADS_2D = (32, 8, 1), 256
+
+
+def parse_launch(text: str, dim: int):
+    """'32x32:160' -> ((32, 32, 1), 160, 0); '16x15x32:256:march' -> (..., 1)."""
+    parts = text.split(":")
+    if len(parts) not in (2, 3) or (len(parts) == 3 and parts[2] != "march"):
+        raise ValueError(f"bad launch {text!r}: expected TILE:THREADS[:march]")
+    tile = tuple(int(x) for x in parts[0].lower().split("x"))
+    if len(tile) != dim:
+        raise ValueError(f"bad launch {text!r}: a {dim}D tile has {dim} extents")
+    if dim == 2:
+        tile = tile + (1,)
+    march = 1 if len(parts) == 3 else 0
+    if march and dim != 3:
+        raise ValueError(f"bad launch {text!r}: the marching kernel is 3D only")
+    return tile, int(parts[1]), march
+
+
+def launch_with(fv, g, tile, threads, march=0):
+    """The default launch of grid g with one tile shape and thread count for
+    all three RK stages."""
+    d = fv.launch_to_dict(fv.fv_default_launch(g if not isinstance(g, list) else g[0]))
+    for st in d["stage"]:
+        st.update(tile=tuple(tile), threads=threads, march=march)
+    return d
 
 
 def kernel_source_hash() -> str:
@@ -178,7 +222,11 @@ def run_ours(args):
     split = args.mode == "split"
     if split and W["batched"]:
         raise SystemExit("--mode split: batched contexts run the fused persistent kernel only")
-    solver = fv.Solver(g, stream=stream, mode=fv.FV_SPLIT if split else None)
+    launch = None
+    if args.launch:
+        tile, thr, march = parse_launch(args.launch, g.dim if not W["batched"] else 2)
+        launch = launch_with(fv, g, tile, thr, march)
+    solver = fv.Solver(g, stream=stream, mode=fv.FV_SPLIT if split else None, launch=launch)
     U = torch.from_numpy(U0).to(dev) if not W["batched"] else solver.pack(
         [torch.from_numpy(u).to(dev) for u in W["states"]])
     if W["batched"]:
@@ -268,7 +316,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded Kelvin-Helmholtz initial condition)",
-        "config": {"workload": W["desc"], "cells": cells, "launch": "default", "launch_params": solver.launch,
+        "config": {"workload": W["desc"], "cells": cells, "launch": args.launch or "default",
+                   "launch_params": solver.launch,
                    "kernel_structure": ("split: per stage %d kernels (limiter and flux per axis, source, RHS, "
                                         "update; Sec. 3.4), intermediates in HBM" % (2 * g.dim + 3)) if split
                    else "fused: one kernel per RK stage",
@@ -302,24 +351,113 @@ def run_ours(args):
             "kernel_fp64_lane_ops_per_s": rate, "frac_of_stream": rate / stream_rate if rate else None}
     if args.workload != "kh4096":
         line["metric"] = W["metric"]
-    if args.tune and not W["batched"]:
-        best, rep = solver.tune(U, samples=args.tune_samples, steps=3, candidates=200000, top=16, rounds=3, refine=2,
-                                exhaustive=1, final_repeats=7, seed=7)
-        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        solver.run(U, args.warmup)
-        torch.cuda.synchronize()
-        e4.record(stream)
-        solver.run(U, args.steps)
-        e5.record(stream)
-        torch.cuda.synchronize()
-        tuned_value = cells * 3 * args.steps / (e4.elapsed_time(e5) / 1e3)
-        line["tuned"] = {"value": tuned_value, "speedup_vs_default": tuned_value / value, "launch": best,
-                         "tuner": {k: v for k, v in rep.items() if k != "exhaustive_best"},
-                         "exhaustive_best": rep["exhaustive_best"]}
+    if world == 1 and not W["batched"] and args.tune_samples > 0:
+        line["tuned"] = tuned_comparison(args, fv, solver, U, g, stream, W)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = W["cpu_baseline"]()
     solver.close()
+    del U
+    if world == 1 and W["name"] == "kh4096" and not split and args.workloads:
+        line["workloads"] = other_workloads(args)
     return line
+
+
+def tuned_comparison(args, fv, solver, U, g, stream, W):
+    """The metric's second half, tuned vs default launch (Sec. 3.4-3.6): run
+    the autotuner on the workload with a bounded sample, then time four
+    launches interleaved -- the naive default (32x8 threads, one cell per
+    thread), the library's default, the search's own pick and the exhaustive
+    best of the reduced space -- each the median of `tune_replays` graph
+    replays of `tune_steps` SSP-RK3 steps (CUDA events on the solver's
+    stream), with clocks sampled during the comparison.  The launch the tuner
+    returns (the fastest of search, default and exhaustive best in its own
+    final timing) is left installed."""
+    import torch
+    default = solver.launch
+    t0 = time.perf_counter()
+    best, rep = solver.tune(U, samples=args.tune_samples, steps=2, candidates=args.tune_candidates, top=16, rounds=3,
+                            refine=1, exhaustive=1, final_repeats=5, seed=7)
+    tuner_s = time.perf_counter() - t0
+    # the naive default: fused 2D kernels at one cell per thread (in the split
+    # structure the library default already is one item per thread)
+    naive = launch_with(fv, g, NAIVE_TILE_2D, NAIVE_THREADS_2D) if g.dim == 2 and args.mode == "fused" else None
+    launches = {"naive_default": naive, "current_default": default, "search": rep["search_best"],
+                "exhaustive_best": rep["exhaustive_best"]}
+    for k in list(launches):
+        if launches[k] is None:
+            del launches[k]
+    times = {k: [] for k in launches}
+    clocks = ClockSampler(gpu_uuid(torch))
+    for _ in range(args.tune_replays):
+        for k, l in launches.items():
+            solver.launch = l
+            solver.run(U, 2)  # captures this launch's graphs; untimed
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.run(U, args.tune_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[k].append(e0.elapsed_time(e1) / args.tune_steps)
+    clk = clocks.stop()
+    solver.launch = best
+    solver.sync()
+    med = {k: statistics.median(v) for k, v in times.items()}
+    cells = g.ncells
+
+    def entry(k):
+        return {"ms_per_step": med[k], "value": cells * 3 / (med[k] / 1e3), "replays_ms_per_step": times[k],
+                "launch": launches[k]}
+
+    out = {
+        "workload": W["name"] + (" (split kernels, the paper's space)" if args.mode == "split" else "") +
+                    "; the state as evolved by the timed run",
+        "unit": UNIT,
+        "current_default": dict(entry("current_default"), note="the library's hand-set default, itself the outcome "
+                                                               "of earlier tuner runs and launch sweeps"),
+        "tuned": dict(entry("search"), note="the FCNN search's own pick (surrogate rounds + refinement)"),
+        "speedup_vs_current_default": med["current_default"] / med["search"],
+        "r2_train": rep["r2_train"], "r2_test": rep["r2_test"],
+        "n_params": rep["n_params"], "space_size": rep["space_size"], "samples": args.tune_samples,
+        "n_train": rep["n_train"], "n_test": rep["n_test"], "n_measured": rep["n_measured"],
+        "n_exhaustive": rep["n_exhaustive"], "candidates_scored": args.tune_candidates, "epochs": rep["epochs"],
+        "tuner_seconds": tuner_s, "returned": ("search", "current_default", "exhaustive_best")[rep["chosen"]],
+        "replays": args.tune_replays, "steps_per_replay": args.tune_steps, "clocks": clk,
+    }
+    if "naive_default" in med:
+        out["naive_default"] = dict(entry("naive_default"), note="32x8 threads, one cell per thread, one CTA per "
+                                                                 "32x8 tile covering the domain")
+        out["speedup_vs_naive_default"] = med["naive_default"] / med["search"]
+    if "exhaustive_best" in med:
+        out["exhaustive_best"] = dict(entry("exhaustive_best"),
+                                      note="best of the reduced space: one tile and thread count for all stages, "
+                                           "box tiles, TMA loads, default time-step kernel")
+        out["vs_exhaustive"] = med["exhaustive_best"] / med["search"]
+        if "naive_default" in med:
+            out["speedup_exhaustive_vs_naive_default"] = med["naive_default"] / med["exhaustive_best"]
+    return out
+
+
+def other_workloads(args):
+    """Short timed runs of the other configurations: 3D Taylor-Green 384^3 and
+    the 96-grid batched Sod set (forward, like the main line, with their own
+    clocks and CPU-oracle baselines) and the adjoint gradient (1024^2 vortex,
+    400 steps, checkpoints every 20)."""
+    out = {}
+    keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "config", "roofline", "clocks",
+            "cpu_baseline", "gpu_launches")
+    for name in ("tgv384", "sod96", "adjoint1024"):
+        a = argparse.Namespace(**vars(args))
+        a.workload, a.n, a.launch, a.mode, a.workloads = name, N_CELLS_SIDE, None, "fused", False
+        a.e2e_steps, a.cpu_seconds, a.tune_samples = 0, args.workload_cpu_seconds, 0
+        if name == "adjoint1024":
+            a.steps, a.warmup = 1, 1
+            ln = run_adjoint(a)
+            out[name] = {k: ln[k] for k in keep + ("adjoint",) if k in ln}
+        else:
+            a.steps, a.warmup = args.workload_steps, 3
+            ln = run_ours(a)
+            out[name] = {k: ln[k] for k in keep if k in ln}
+    return out
 
 
 def make_workload(args, I):
@@ -578,8 +716,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=("fused", "split"), default="fused",
                     help="kernel structure: fused (one kernel per RK stage) or split (the paper's per-stage kernels)")
-    ap.add_argument("--tune", action="store_true", help="also run the autotuner and time its launch")
-    ap.add_argument("--tune-samples", type=int, default=1000)
+    ap.add_argument("--launch", default=None,
+                    help="TILE:THREADS[:march] for all three RK stages (e.g. 32x8:256) instead of the default launch")
+    ap.add_argument("--tune-samples", type=int, default=300,
+                    help="random launches the autotuner times for the tuned comparison (0: no tuned object)")
+    ap.add_argument("--tune-candidates", type=int, default=1000000,
+                    help="random launches the trained network scores")
+    ap.add_argument("--tune-replays", type=int, default=7)
+    ap.add_argument("--tune-steps", type=int, default=5)
+    ap.add_argument("--no-workloads", dest="workloads", action="store_false",
+                    help="skip the short runs of the other configurations")
+    ap.add_argument("--workload-steps", type=int, default=5)
+    ap.add_argument("--workload-cpu-seconds", type=float, default=5.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

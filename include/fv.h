@@ -306,6 +306,7 @@ typedef struct fv_tune_report {
   int rounds, n_refined;  /* surrogate rounds run; measurements made by the refinement */
   int chosen;             /* the returned launch: 0 the search's, 1 the default, 2 the exhaustive best */
   fv_launch exhaustive_best;
+  fv_launch search_best;  /* the best launch the search itself found (timed as t_search) */
 } fv_tune_report;
 
 /* Tune the launch configuration of ctx for the state U (device or host; not
@@ -346,17 +347,22 @@ int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts, fv_launch *b
  * mode is valid and both pointers are non-NULL. */
 int fv_tune_space(int dim, int mode, int *n_params, double *size);
 
-/* Residual R_h of Eq. (5) and, if rnorm2 != NULL, sum over cells of R_v^2 per
- * variable -- the same values as fv_residual -- without a context and without
- * allocating anything.  The paper has no counterpart: this is a facility for
- * callers that cannot allocate device memory when they call (code running
- * while a stream is being captured, where cudaMalloc is not allowed; services
- * that fix their device-memory budget at start-up; hosts that cannot afford
- * the device-wide synchronisation cudaFree implies).
+/* The residual and, if rnorm2 != NULL, sum over cells of R_v^2 per variable,
+ * without a context and without allocating anything: the values fv_residual
+ * returns on a context created with the same grid and scheme and no source
+ * set (S = 0).  The paper has no counterpart: this is a facility for callers
+ * that cannot allocate device memory when they call -- services that fix
+ * their device-memory budget at start-up, plug-ins running inside an
+ * application that owns the device's memory, hosts that cannot afford the
+ * device-wide synchronisation cudaFree implies.
  * U, R (nvar*ncells doubles, R not aliasing U) and rnorm2 (nvar doubles) are
- * caller-owned DEVICE pointers; host pointers return FV_EINVAL.  The default
- * launch configuration is used, with plain tile loads.  Stream-ordered on
- * `stream` (a cudaStream_t, NULL = legacy default); returns without waiting.
+ * caller-owned DEVICE pointers of the current GPU (or managed memory); host
+ * pointers and memory of another GPU return FV_EINVAL.  The default launch
+ * configuration is used, with plain tile loads.  Stream-ordered on `stream`
+ * (a cudaStream_t, NULL = legacy default); returns without waiting.  Like
+ * fv_residual it does not test the state: a non-physical U (rho <= 0, p <= 0,
+ * NaN) gives a non-physical R, and nothing reports it (the time-step
+ * reduction of a context is what flags such cells).
  * Scratch: a fixed array of 131072 + 32 doubles (1 MiB + 256 B) in the
  * library's device image -- every GPU that loads libfv holds it until the
  * process exits -- holding nvar partial sums per tile.  With rnorm2 != NULL
@@ -365,7 +371,7 @@ int fv_tune_space(int dim, int mode, int *n_params, double *size);
  * grids return FV_EINVAL before anything is launched.  The first call on each
  * device looks up the scratch array's device address (cudaGetSymbolAddress)
  * and sets kernel attributes: make that first call before any stream capture.
- * Every call reuses the same scratch (the flags word is cleared by each call,
+ * Every call reuses the same scratch (a flags word is cleared by each call,
  * the partials are rewritten), so calls that may overlap on the GPU -- on
  * different streams without ordering, or from several threads -- race and
  * must be serialised by the caller. */

@@ -49,14 +49,43 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool is_device_ptr(const void *p) {
+
+}  // namespace
+
+namespace fvk {
+
+int validate_grid(const fv_grid *g) {
+  if (!g || (g->dim != 2 && g->dim != 3)) return FV_EINVAL;
+  for (int d = 0; d < 3; ++d) {
+    const bool active = d < g->dim;
+    if (active) {
+      if (g->n[d] < 1 || !(g->len[d] > 0.0)) return FV_EINVAL;
+      for (int s = 0; s < 2; ++s)
+        if (g->bc[d][s] != FV_BC_PERIODIC && g->bc[d][s] != FV_BC_TRANSMISSIVE) return FV_EINVAL;
+      if ((g->bc[d][0] == FV_BC_PERIODIC) != (g->bc[d][1] == FV_BC_PERIODIC)) return FV_EINVAL;
+    } else if (g->n[d] != 1) {
+      return FV_EINVAL;
+    }
+  }
+  const long long cells = (long long)g->n[0] * g->n[1] * g->n[2];
+  if (cells * (g->dim + 2) >= (1ll << 40)) return FV_EINVAL;
+  return FV_OK;
+}
+
+PtrKind pointer_kind(const void *p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     (void)cudaGetLastError();
-    return false;
+    return PTR_HOST;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+  if (at.type == cudaMemoryTypeDevice) return at.device == dev ? PTR_DEVICE : PTR_OTHER_DEVICE;
+  return PTR_HOST;
 }
+
+}  // namespace fvk
+
+namespace {
 
 struct GraphEntry {
   const double *U;
@@ -114,22 +143,12 @@ namespace {
 // norm reduction buffer, 5 x 32 doubles), kept free of the dynamic budget.
 constexpr size_t kStaticSmemReserve = 2048;
 
-int validate_grid(const fv_grid *g) {
-  if (!g || (g->dim != 2 && g->dim != 3)) return FV_EINVAL;
-  for (int d = 0; d < 3; ++d) {
-    const bool active = d < g->dim;
-    if (active) {
-      if (g->n[d] < 1 || !(g->len[d] > 0.0)) return FV_EINVAL;
-      for (int s = 0; s < 2; ++s)
-        if (g->bc[d][s] != FV_BC_PERIODIC && g->bc[d][s] != FV_BC_TRANSMISSIVE) return FV_EINVAL;
-      if ((g->bc[d][0] == FV_BC_PERIODIC) != (g->bc[d][1] == FV_BC_PERIODIC)) return FV_EINVAL;
-    } else if (g->n[d] != 1) {
-      return FV_EINVAL;
-    }
-  }
-  const long long cells = (long long)g->n[0] * g->n[1] * g->n[2];
-  if (cells * (g->dim + 2) >= (1ll << 40)) return FV_EINVAL;
-  return FV_OK;
+// *host: whether p is host memory (staged by the call).  FV_EINVAL for memory
+// of a GPU other than the context's.
+int where(const fv_ctx *c, const void *p, bool *host) {
+  const PtrKind k = pointer_kind(p, c->device);
+  *host = k == PTR_HOST;
+  return k == PTR_OTHER_DEVICE ? FV_EINVAL : FV_OK;
 }
 
 int validate_scheme(const fv_scheme *s) {
@@ -764,7 +783,7 @@ int fv_set_launch(fv_ctx *c, const fv_launch *l) {
 int fv_set_source(fv_ctx *c, const double *S) {
   if (!c) return FV_EINVAL;
   if (c->ngrids > 1) return FV_EUNSUPPORTED;
-  if (S && !is_device_ptr(S)) return FV_EINVAL;
+  if (S && pointer_kind(S, c->device) != PTR_DEVICE) return FV_EINVAL;
   if (S != c->source) {
     FV_CK(cudaStreamSynchronize(c->stream));  // launches queued with the old source finish first
     drop_graphs(c);                           // captured graphs hold the old pointer
@@ -783,8 +802,8 @@ int fv_residual(fv_ctx *c, const double *U, double *R, double *rnorm2) {
   if (!c || !U || !R || U == R) return FV_EINVAL;
   if (c->ngrids > 1) return FV_EUNSUPPORTED;
   int r;
-  const bool hostU = !is_device_ptr(U), hostR = !is_device_ptr(R);
-  const bool hostN = rnorm2 && !is_device_ptr(rnorm2);
+  bool hostU, hostR, hostN = false;
+  if (where(c, U, &hostU) || where(c, R, &hostR) || (rnorm2 && where(c, rnorm2, &hostN))) return FV_EINVAL;
   if ((hostU || hostR) && (r = ensure_staging(c))) return r;
   const double *Ud = U;
   double *Rd = R;
@@ -830,7 +849,8 @@ int fv_time_step(fv_ctx *c, const double *U, double *dt_out) {
   if (!c || !U || !dt_out) return FV_EINVAL;
   if (c->ngrids > 1) return FV_EUNSUPPORTED;
   int r;
-  const bool hostU = !is_device_ptr(U), hostD = !is_device_ptr(dt_out);
+  bool hostU, hostD;
+  if (where(c, U, &hostU) || where(c, dt_out, &hostD)) return FV_EINVAL;
   const double *Ud = U;
   if (hostU) {
     if ((r = ensure_staging(c))) return r;
@@ -855,7 +875,8 @@ int fv_rk_step(fv_ctx *c, double *U, double dt, double *dt_used) {
   if (!c || !U) return FV_EINVAL;
   if (c->ngrids > 1) return fv_run(c, U, 1, dt, dt_used);
   int r;
-  const bool hostU = !is_device_ptr(U);
+  bool hostU;
+  if (where(c, U, &hostU)) return FV_EINVAL;
   double *Ud = U;
   if (hostU) {
     if ((r = ensure_staging(c))) return r;
@@ -927,7 +948,8 @@ int last_step_to_host(fv_ctx *c, double *Ud, double *Uh, double dt_fixed, bool c
 int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
   if (!c || !U || nsteps < 0) return FV_EINVAL;
   int r;
-  const bool hostU = !is_device_ptr(U);
+  bool hostU;
+  if (where(c, U, &hostU)) return FV_EINVAL;
   double *Ud = U;
   if (hostU) {
     if ((r = ensure_staging(c))) return r;
@@ -1053,7 +1075,9 @@ extern "C" int fv_adjoint_vjp(fv_ctx *c, int what, const double *U, const double
   if (!c || !U || !lam || !out || out == U || out == lam) return FV_EINVAL;
   if (c->ngrids > 1 || c->scheme.limiter != FV_LIM_MINMOD || c->scheme.recon != FV_RECON_CONSERVED)
     return FV_EUNSUPPORTED;
-  if (!is_device_ptr(U) || !is_device_ptr(lam) || !is_device_ptr(out)) return FV_EINVAL;
+  if (pointer_kind(U, c->device) != PTR_DEVICE || pointer_kind(lam, c->device) != PTR_DEVICE ||
+      pointer_kind(out, c->device) != PTR_DEVICE)
+    return FV_EINVAL;
   if (what == FV_VJP_RESIDUAL) return adjoint(c, U, lam, out, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr, 0.0);
   if (what != FV_VJP_RKSTEP || !(dt > 0.0)) return FV_EINVAL;
   if (!c->X1) FV_CK(cudaMalloc(&c->X1, c->state_bytes));

@@ -294,11 +294,13 @@ __device__ __forceinline__ void roe_F(const double (&QL)[NT + 3], const double (
   const double alpha = (fma(-(rho * sc), dun, dp) * tc) * half_nonneg(tc);  // (dp -+ rho~ c~ du_n) / (2 c~^2)
   const double x = aun - c;
   // k = (x - |x|*)/2 with the entropy fix.  Whether |x| < delta = efix c~ is
-  // decided in FP32 (operands truncated on the integer pipe): the fixed |x|
-  // equals delta at |x| = delta, so a decision flipped within FP32
-  // resolution changes the flux by O(((|x| - delta) / delta)^2 delta), below
-  // FP64 rounding.  Near sonic points only: a warp-uniform branch keeps the
-  // (rare) fix from being computed unconditionally.
+  // decided in FP32 (operands truncated on the integer pipe).  The fixed |x|
+  // equals delta at |x| = delta and differs from |x| by (|x| - delta)^2 /
+  // (2 delta), and FP32 truncation can only flip the decision where
+  // | |x|/delta - 1 | < ~2^-22, so a flipped decision changes k by at most
+  // ~delta 2^-46: about a hundred FP64 roundings of k, far below the 1e-12
+  // the results are held to.  Near sonic points only: a warp-uniform branch
+  // keeps the (rare) fix from being computed unconditionally.
   double k = min0(x);
   const float deltaf = __fmul_rn(f32_trunc(efix), f32_trunc(c));
   const bool fix = f32_trunc(iabs(x)) < deltaf;

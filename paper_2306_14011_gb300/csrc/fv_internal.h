@@ -3,6 +3,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "../../include/fv.h"
+
 namespace fvk {
 
 // Largest CTA of the 3D box-tiled stage kernel (its register budget).
@@ -173,6 +175,16 @@ cudaError_t launch_debug_wait(int kind, unsigned long long limit_ns, unsigned *w
 // Raise the stage kernels' dynamic shared-memory limit to the device maximum
 // (smem_optin = cudaDeviceProp::sharedMemPerBlockOptin of the current device).
 cudaError_t stage_kernel_attributes(int dim, size_t smem_optin);
+
+// Argument checks shared by the entry points (fv_api.cu).
+// validate_grid: FV_OK or FV_EINVAL (dimension, extents, boundary pairs, size).
+int validate_grid(const fv_grid *g);
+// Where a caller's array lives: host memory (pageable or pinned; the call
+// stages it), memory of device `dev` or managed memory (used in place), or
+// memory of another GPU (rejected: the kernels would reach it only through
+// peer access).
+enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1, PTR_OTHER_DEVICE = 2 };
+PtrKind pointer_kind(const void *p, int dev);
 
 }  // namespace fvk
 

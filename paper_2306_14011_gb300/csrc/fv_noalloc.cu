@@ -1,10 +1,10 @@
 // fv_residual_noalloc: the residual and its norms without any allocation.
 //
-// For callers that cannot allocate device memory at the time they call --
-// code running while a stream is being captured (cudaMalloc is not allowed
-// there), services that fix their device-memory budget at start-up, or hosts
-// that cannot afford the device-wide synchronisation cudaFree implies -- and
-// therefore cannot create an fv_ctx.  The only scratch the residual needs,
+// For callers that cannot allocate device memory at the time they call, and
+// therefore cannot create an fv_ctx: services that fix their device-memory
+// budget at start-up, plug-ins running inside an application that owns the
+// device's memory, or hosts that cannot afford the device-wide
+// synchronisation cudaFree implies.  The only scratch the residual needs,
 // the per-CTA partial sums of R_v^2, lives in a fixed array below.
 #include <cstring>
 #include <mutex>
@@ -60,39 +60,23 @@ int setup_device(int dev, double **scratch) {
   return FV_OK;
 }
 
-bool device_pointer(const void *p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-bool grid_ok(const fv_grid *g) {
-  if (!g || (g->dim != 2 && g->dim != 3)) return false;
-  for (int d = 0; d < 3; ++d) {
-    if (d < g->dim) {
-      if (g->n[d] < 1 || !(g->len[d] > 0.0)) return false;
-      for (int s = 0; s < 2; ++s)
-        if (g->bc[d][s] != FV_BC_PERIODIC && g->bc[d][s] != FV_BC_TRANSMISSIVE) return false;
-      if ((g->bc[d][0] == FV_BC_PERIODIC) != (g->bc[d][1] == FV_BC_PERIODIC)) return false;
-    } else if (g->n[d] != 1) {
-      return false;
-    }
-  }
-  return (long long)g->n[0] * g->n[1] * g->n[2] * (g->dim + 2) < (1ll << 40);
-}
-
 }  // namespace
 
 extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const double *U, double *R,
                                    double *rnorm2, void *stream) {
-  if (!grid_ok(g) || !s || !(s->gamma > 1.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0) ||
+  if (validate_grid(g) != FV_OK || !s || !(s->gamma > 1.0) || !(s->eps >= 0.0) || !(s->eps <= 2.0) || !(s->efix >= 0.0) ||
       !(s->efix < 1.0) || s->limiter < FV_LIM_MINMOD || s->limiter > FV_LIM_NONE ||
       (s->recon != FV_RECON_CONSERVED && s->recon != FV_RECON_PRIMITIVE))
     return FV_EINVAL;
-  if (!U || !R || U == R || !device_pointer(U) || !device_pointer(R) || (rnorm2 && !device_pointer(rnorm2)))
+  if (!U || !R || U == R) return FV_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return FV_ECUDA;
+  }
+  // device (or managed) memory of the current GPU only
+  if (pointer_kind(U, dev) != PTR_DEVICE || pointer_kind(R, dev) != PTR_DEVICE ||
+      (rnorm2 && pointer_kind(rnorm2, dev) != PTR_DEVICE))
     return FV_EINVAL;
   fv_launch l;
   if (fv_default_launch(g, &l) != FV_OK) return FV_EINVAL;
@@ -103,17 +87,14 @@ extern "C" int fv_residual_noalloc(const fv_grid *g, const fv_scheme *s, const d
   const long long nblk = (long long)nt[0] * nt[1] * nt[2];
   if (nblk >= (1ll << 31)) return FV_EINVAL;
   if (rnorm2 && nblk * nv > kPartials) return FV_EINVAL;  // grid too large for the fixed scratch
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return FV_ECUDA;
-  }
   double *scratch = nullptr;
   int r = setup_device(dev, &scratch);
   if (r) return r;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The flags word is where a kernel would raise a timed-out tile-load wait;
+  // plain tile loads have no such wait, and nothing reads it back.  It must
+  // start at zero; the partials are all rewritten by this call.
   unsigned *flags = reinterpret_cast<unsigned *>(scratch);
-  // the flags word must start at zero; the partials are all rewritten by this call
   if (cudaMemsetAsync(flags, 0, sizeof(unsigned), st) != cudaSuccess) {
     (void)cudaGetLastError();
     return FV_ECUDA;

@@ -561,6 +561,7 @@ extern "C" int fv_tune(fv_ctx *ctx, const double *U, const fv_tune_opts *opts_in
     rep->rounds = rounds_run;
     rep->n_refined = n_refined;
     rep->exhaustive_best = exh_best;
+    rep->search_best = tuned;
   }
   return FV_OK;
 }

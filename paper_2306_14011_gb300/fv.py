@@ -77,7 +77,8 @@ class fv_tune_report(C.Structure):
                 ("t_best_sampled", C.c_double), ("t_exhaustive", C.c_double), ("r2_train", C.c_double),
                 ("r2_test", C.c_double), ("space_size", C.c_double), ("n_params", C.c_int), ("n_train", C.c_int),
                 ("n_test", C.c_int), ("epochs", C.c_int), ("n_measured", C.c_int), ("n_exhaustive", C.c_int),
-                ("rounds", C.c_int), ("n_refined", C.c_int), ("chosen", C.c_int), ("exhaustive_best", fv_launch)]
+                ("rounds", C.c_int), ("n_refined", C.c_int), ("chosen", C.c_int), ("exhaustive_best", fv_launch),
+                ("search_best", fv_launch)]
 
 
 _lib = None
@@ -293,8 +294,10 @@ def fv_destroy(ctx: int):
 
 def fv_residual_noalloc(g, scheme: fv_scheme, U, R, rnorm2=None, stream=None):
     """Residual (and norms) without a context and without allocating: for
-    callers that cannot allocate device memory when they call (e.g. while a
-    stream is being captured).  Device tensors only; grids above the fixed
+    callers that cannot allocate device memory when they call (a fixed
+    device-memory budget, a host application that owns the device's memory).
+    Equals fv_residual on a context with the same grid and scheme and no
+    source.  Device tensors of the current GPU only; grids above the fixed
     scratch limit raise FvError(FV_EINVAL).  Calls sharing the GPU must not
     overlap (they share one scratch array)."""
     _check(load().fv_residual_noalloc(C.byref(make_grid(g)), C.byref(scheme), _ptr(U), _ptr(R),
@@ -348,8 +351,10 @@ def fv_tune(ctx: int, U, **opts):
     best = fv_launch()
     rep = fv_tune_report()
     _check(load().fv_tune(ctx, _ptr(U), C.byref(o), C.byref(best), C.byref(rep)), "fv_tune")
-    report = {f[0]: getattr(rep, f[0]) for f in fv_tune_report._fields_ if f[0] != "exhaustive_best"}
+    report = {f[0]: getattr(rep, f[0]) for f in fv_tune_report._fields_
+              if f[0] not in ("exhaustive_best", "search_best")}
     report["exhaustive_best"] = launch_to_dict(rep.exhaustive_best) if rep.n_exhaustive else None
+    report["search_best"] = launch_to_dict(rep.search_best)
     return launch_to_dict(best), report
 
 

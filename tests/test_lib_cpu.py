@@ -116,13 +116,3 @@ def test_debug_wait_rejects_bad_arguments_on_the_host():
         with pytest.raises(fv.FvError) as e:
             fv.fv_debug_wait(kind, limit, stream=0)
         assert e.value.status == fv.FV_EINVAL
-
-
-def test_sweep_configuration_parsing():
-    from paper_2306_14011_gb300.sweep import parse_config
-    assert parse_config("32x32:160", 2) == ((32, 32, 1), 160, 0)
-    assert parse_config("8x8x8:192", 3) == ((8, 8, 8), 192, 0)
-    assert parse_config("16x15x32:256:march", 3) == ((16, 15, 32), 256, 1)
-    for bad, dim in [("32x32", 2), ("32:160", 2), ("8x8x8:192", 2), ("32x32:160:march", 2), ("8x8:1:box", 3)]:
-        with pytest.raises(ValueError):
-            parse_config(bad, dim)

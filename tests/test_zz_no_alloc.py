@@ -1,10 +1,10 @@
 """The allocation-free residual entry point, fv_residual_noalloc.
 
 Some callers cannot allocate device memory when they call into the library
-(code running under stream capture, fixed-budget services, hosts that cannot
-take cudaFree's device-wide synchronisation); for them the residual and its
-norms are available without a context, using a fixed scratch array inside the
-library.  These tests check it against fv_residual (through a context) on
+(services with a fixed device-memory budget, plug-ins inside an application
+that owns the device's memory, hosts that cannot take cudaFree's device-wide
+synchronisation); for them the residual and its norms are available without a
+context, using a fixed scratch array inside the library.  These tests check it against fv_residual (through a context) on
 consecutive calls that share that scratch.  This file is collected last, so a
 run that stops at the first failure has already run every other test.
 """
