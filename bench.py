@@ -108,7 +108,8 @@ def kernel_source_hash() -> str:
     """Hash of the stage kernel's code (comments and blank lines removed, so a
     comment edit does not retire a recorded measurement)."""
     h = hashlib.sha256()
-    for f in ("fv_stage.cuh", "fv_device.cuh", "fv_internal.h", "fv_stage2d.cu", "fv_stage3d.cu"):
+    for f in ("fv_stage.cuh", "fv_device.cuh", "fv_emu.h", "fv_internal.h", "fv_stage2d.cu", "fv_stage2d_wide.cu",
+              "fv_stage3d.cu"):
         with open(os.path.join(ROOT, "paper_2306_14011_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].strip()

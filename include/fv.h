@@ -145,8 +145,9 @@ typedef struct fv_launch {
 typedef struct fv_ctx fv_ctx;
 
 /* Fill *l with the default launch configuration for grid g (one tile shape
- * and thread count for all stages): mode FV_FUSED; 2D 32x32 box tiles with
- * 160 threads (256 in a batched context created without a launch); 3D
+ * and thread count for all stages): mode FV_FUSED; 2D 64x16 box tiles with
+ * 192 threads (32x32 tiles with 256 threads in a batched context created
+ * without a launch); 3D
  * 8x8x8 box tiles with 192 threads; time-step reduction 512 threads, four
  * CTAs per SM; split kernels 128 threads, grid 0 (one item per thread: the
  * analogue of a directive compiler's default vector length and gang count).
@@ -396,8 +397,10 @@ int fv_debug_fp64_rate(int kind, double *lane_ops_per_s, void *stream);
 /* The kernels' integer-pipe replacements of FP64 operations, applied to n
  * device doubles (for tests): out[i] = op(x[i], y[i]) with op 0: x/2 for
  * x >= 0 (half_nonneg), 1: x/4, 2: x/2, 3: 2x (exponent shifts), 4:
- * minmod(x, y), 5: |x|.  Each must equal its FP64 definition bit for bit.
- * y is read only by op 4.  Stream-ordered, no synchronisation.  FV_EINVAL
+ * minmod(x, y), 5: |x|, 6: x * y (the product on 32-bit integer operations
+ * the flux kernels use, with the FP64 multiplier for operands or results off
+ * its path), 7: the same with signed zeros on the integer path.  Each must
+ * equal its FP64 definition bit for bit.  y is read only by ops 4, 6 and 7.  Stream-ordered, no synchronisation.  FV_EINVAL
  * for a bad op or pointer. */
 int fv_debug_bits(int op, const double *x, const double *y, double *out, long n, void *stream);
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfv.so")
-SOURCES = ["fv_api.cu", "fv_reduce.cu", "fv_stage2d.cu", "fv_stage3d.cu", "fv_noalloc.cu", "fv_mlp.cu",
+SOURCES = ["fv_api.cu", "fv_reduce.cu", "fv_stage2d.cu", "fv_stage2d_wide.cu", "fv_stage3d.cu", "fv_noalloc.cu", "fv_mlp.cu",
            "fv_tune.cu", "fv_batch.cu", "fv_adjoint.cu", "fv_march.cu", "fv_split.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -673,17 +673,18 @@ int fv_default_launch(const fv_grid *g, fv_launch *l) {
   for (int s = 0; s < 3; ++s) {
     fv_kernel_cfg &k = l->stage[s];
     if (g->dim == 2) {
-      k.tile[0] = 32;  // the largest tile with two CTAs per SM (shared memory)
-      k.tile[1] = 32;
+      k.tile[0] = 64;  // two CTAs per SM (shared memory)
+      k.tile[1] = 16;
       k.tile[2] = 1;
     } else {
       k.tile[0] = 8;  // 9 x 8 x 8 faces per axis: three full rounds of 192 threads
       k.tile[1] = 8;
       k.tile[2] = 8;
     }
-    // 2D: 160 threads split the 33 faces of each of the 32 lines of a 32x32
-    // tile into runs of 7 (5 runs per line), one run per thread
-    k.threads = g->dim == 2 ? 160 : 192;
+    // 2D: 192 threads take the 17 faces of each of the 64 y-lines of a 64x16
+    // tile in runs of 6 (one run per thread) and the 65 faces of each of its
+    // 16 x-lines in 11 runs of 6 or fewer
+    k.threads = 192;
     k.grid = 0;
   }
   l->dt.threads = 512;  // 1024 threads per SM keep enough loads in flight
@@ -727,10 +728,13 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
   } else {
     fv_default_launch(&c->grid, &c->launch);
     // the batched persistent kernel also runs its CFL phases with these
-    // threads: it keeps 256 per CTA (measured 8% faster than 160 on the
-    // 96-grid Sod batch)
+    // threads: it keeps 32x32 tiles and 256 threads per CTA (measured 8%
+    // faster than 160 on the 96-grid Sod batch)
     if (ngrids > 1)
-      for (int s = 0; s < 3; ++s) c->launch.stage[s].threads = 256;
+      for (int s = 0; s < 3; ++s) {
+        c->launch.stage[s].tile[0] = c->launch.stage[s].tile[1] = 32;
+        c->launch.stage[s].threads = 256;
+      }
   }
   if ((r = validate_launch(&c->grid, &c->scheme, &c->launch, c->smem_optin))) return fail(r);
   if (ngrids > 1 && c->launch.mode != FV_FUSED) return fail(FV_EUNSUPPORTED);
@@ -1146,7 +1150,7 @@ int fv_debug_wait(int kind, double limit_seconds, void *stream) {
 }
 
 int fv_debug_bits(int op, const double *x, const double *y, double *out, long n, void *stream) {
-  if (op < 0 || op > 5 || !x || !out || n < 0 || (op == 4 && !y)) return FV_EINVAL;
+  if (op < 0 || op > 7 || !x || !out || n < 0 || ((op == 4 || op >= 6) && !y)) return FV_EINVAL;
   FV_CK(launch_debug_bits(op, x, y, out, n, static_cast<cudaStream_t>(stream)));
   return FV_OK;
 }

@@ -11,11 +11,17 @@
 //     special-function unit, relative error below 2^-20) and are refined to
 //     full double precision by one third-order Householder step in FMA;
 //   * the Roe flux is arranged so each quantity is formed once, and evaluated
-//     one-sided (roe_F), without the flux of the right state.
+//     one-sided (roe_F), without the flux of the right state;
+//   * its products run on the integer pipe (pmul, fv_emu.h: the correctly
+//     rounded product in 32-bit integer operations), which the FP64 pipe's
+//     own work leaves idle; a warp whose operands leave that path evaluates
+//     the flux again in FP64.
 #pragma once
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include "fv_emu.h"
 
 namespace fvk {
 
@@ -101,6 +107,23 @@ __device__ __forceinline__ bool not_positive_finite(double x) {
   return ix <= 0 || ix >= 0x7ff0000000000000ll;
 }
 
+// ------------------------------------------------------------ products on the integer pipe
+// a * b in the flux routines.  EMU: on the integer pipe without a branch --
+// ok is cleared when the operands or the product leave the integer path
+// (the value is then meaningless and the caller recomputes in FP64); ZERO
+// also takes signed zeros on the integer path.  Otherwise the FP64 product,
+// rounded on its own (__dmul_rn: never contracted into a neighbouring
+// addition), so that both evaluations give the same bits.
+template <bool EMU, bool ZERO = false>
+__device__ __forceinline__ double pmul(double a, double b, bool &ok) {
+  if (!EMU) return __dmul_rn(a, b);
+  uint32_t hr, lr;
+  const uint32_t ha = (uint32_t)__double2hiint(a), la = (uint32_t)__double2loint(a);
+  const uint32_t hb = (uint32_t)__double2hiint(b), lb = (uint32_t)__double2loint(b);
+  ok &= ZERO ? emu_dmul_bits_z(ha, la, hb, lb, hr, lr) : emu_dmul_bits(ha, la, hb, lb, hr, lr);
+  return __hiloint2double((int)hr, (int)lr);
+}
+
 // ------------------------------------------------------------ reciprocal and rsqrt
 __device__ __forceinline__ double rsqrt_seed(double x) {
   double y;
@@ -117,13 +140,18 @@ __device__ __forceinline__ double rcp_seed(double x) {
 // 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)); truncating
 // the binomial series after e^2 is the third-order Householder step, so
 // |e| < 2^-20 leaves a truncation error below 2^-59 (5 FP64 operations).
-__device__ __forceinline__ double rsqrt_fp64(double x) {
+template <bool EMU = false>
+__device__ __forceinline__ double rsqrt_fp64(double x, bool &ok) {
   const double y = rsqrt_seed(x);
-  const double t = x * y;
+  const double t = pmul<EMU>(x, y, ok);
   const double e = fma(-t, y, 1.0);
   const double c = fma(e, 0.375, 0.5);
-  const double ye = y * e;
+  const double ye = pmul<EMU, true>(y, e, ok);  // e is exactly 0 for an exact seed
   return fma(ye, c, y);
+}
+__device__ __forceinline__ double rsqrt_fp64(double x) {
+  bool ok = true;
+  return rsqrt_fp64<false>(x, ok);
 }
 
 // 1/x for normal x: 1/x = y0 / (1 - e) with e = 1 - x*y0, so
@@ -233,65 +261,69 @@ __device__ __forceinline__ double ineg(double x) {
 // H~ - c~ |u~_n|) (upper signs for u~_n >= 0).  Free streams give F(Q)
 // exactly; fully supersonic faces give the upwind physical flux exactly.
 // g1 = gamma - 1; inv2efix = 1 / (2 efix) (unused when efix = 0); efix < 1.
-template <int NT>
-__device__ __forceinline__ void roe_F(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
-                                      double efix, double inv2efix, double (&G)[NT + 3]) {
+// EMU: the products run on the integer pipe (pmul) and ok reports whether
+// every one stayed on the integer path; the wrapper roe_F below recomputes
+// the flux in FP64 when one did not.
+template <int NT, bool EMU>
+__device__ __forceinline__ void roe_F_impl(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
+                                           double efix, double inv2efix, double (&G)[NT + 3], bool &ok) {
   constexpr int E = NT + 2;
   // left primitives: 1/sqrt(rho) gives both sqrt(rho) and 1/rho
-  const double tL = rsqrt_fp64(QL[0]);
-  const double rL = tL * tL;
-  const double sL = QL[0] * tL;
-  const double unL = QL[1] * rL;
+  const double tL = rsqrt_fp64<EMU>(QL[0], ok);
+  const double rL = pmul<EMU>(tL, tL, ok);
+  const double sL = pmul<EMU>(QL[0], tL, ok);
+  const double unL = pmul<EMU, true>(QL[1], rL, ok);
   double utL[NT];
-  double kL = QL[1] * unL;  // rho |u|^2
+  double kL = pmul<EMU, true>(QL[1], unL, ok);  // rho |u|^2
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    utL[t] = QL[2 + t] * rL;
+    utL[t] = pmul<EMU, true>(QL[2 + t], rL, ok);
     kL = fma(QL[2 + t], utL[t], kL);
   }
-  const double pL = g1 * fma(-0.5, kL, QL[E]);
+  const double pL = pmul<EMU>(g1, fma(-0.5, kL, QL[E]), ok);
   const double eL = QL[E] + pL;  // rho h_t
   // right primitives
-  const double tR = rsqrt_fp64(QR[0]);
-  const double rR = tR * tR;
-  const double sR = QR[0] * tR;
-  const double unR = QR[1] * rR;
+  const double tR = rsqrt_fp64<EMU>(QR[0], ok);
+  const double rR = pmul<EMU>(tR, tR, ok);
+  const double sR = pmul<EMU>(QR[0], tR, ok);
+  const double unR = pmul<EMU, true>(QR[1], rR, ok);
   double utR[NT];
-  double kR = QR[1] * unR;
+  double kR = pmul<EMU, true>(QR[1], unR, ok);
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    utR[t] = QR[2 + t] * rR;
+    utR[t] = pmul<EMU, true>(QR[2 + t], rR, ok);
     kR = fma(QR[2 + t], utR[t], kR);
   }
-  const double pR = g1 * fma(-0.5, kR, QR[E]);
+  const double pR = pmul<EMU>(g1, fma(-0.5, kR, QR[E]), ok);
   const double eR = QR[E] + pR;
 
   // Roe averages with sqrt(rho) weights wL = sL / (sL + sR), wR = 1 - wL:
   // u~ = uR - wL (uR - uL), and H~ = (sL HL + sR HR) / (sL + sR) with
   // sL HL = eL / sL = eL tL
   const double inv = rcp_fp64(sL + sR);
-  const double wL = sL * inv;
+  const double wL = pmul<EMU>(sL, inv, ok);
   const double dun = unR - unL;
   const double un = fma(-wL, dun, unR);
   double ut[NT];
-  double q2 = un * un;
+  double q2 = pmul<EMU, true>(un, un, ok);
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     ut[t] = fma(-wL, utR[t] - utL[t], utR[t]);
     q2 = fma(ut[t], ut[t], q2);
   }
-  const double H = fma(eL, tL, eR * tR) * inv;
-  const double rho = sL * sR;
-  const double c2 = g1 * (H - half_nonneg(q2));
-  const double tc = rsqrt_fp64(c2);  // 1/c~
-  const double c = c2 * tc;
+  const double H = pmul<EMU>(fma(eL, tL, pmul<EMU>(eR, tR, ok)), inv, ok);
+  const double rho = pmul<EMU>(sL, sR, ok);
+  const double c2 = pmul<EMU>(g1, H - half_nonneg(q2), ok);
+  const double tc = rsqrt_fp64<EMU>(c2, ok);  // 1/c~
+  const double c = pmul<EMU>(c2, tc, ok);
 
   // the acoustic wave that crosses from downwind (upper signs: u~_n >= 0)
   const bool up_left = __double2hiint(un) >= 0;
   const double aun = iabs(un);
   const double sc = isel(up_left, c, ineg(c));
   const double dp = pR - pL;
-  const double alpha = (fma(-(rho * sc), dun, dp) * tc) * half_nonneg(tc);  // (dp -+ rho~ c~ du_n) / (2 c~^2)
+  const double alpha =
+      pmul<EMU, true>(pmul<EMU, true>(fma(-pmul<EMU>(rho, sc, ok), dun, dp), tc, ok), half_nonneg(tc), ok);  // (dp -+ rho~ c~ du_n) / (2 c~^2)
   const double x = aun - c;
   // k = (x - |x|*)/2 with the entropy fix.  Whether |x| < delta = efix c~ is
   // decided in FP32 (operands truncated on the integer pipe).  The fixed |x|
@@ -309,16 +341,28 @@ __device__ __forceinline__ void roe_F(const double (&QL)[NT + 3], const double (
     const double d2 = delta * delta, s4 = 0.5 * (tc * inv2efix);  // s4 = 1 / (4 delta)
     k = isel(fix, fma(-fma(x, x, d2), s4, 0.5 * x), k);
   }
-  const double g = k * alpha;
+  const double g = pmul<EMU, true>(k, alpha, ok);
 
   // F(Q_upwind) + g r_s (selects on the integer pipe)
   const double m = isel(up_left, QL[1], QR[1]);
   const double u_n = isel(up_left, unL, unR);
   G[0] = m + g;
-  G[1] = fma(m, u_n, isel(up_left, pL, pR) + g * (un - sc));
+  G[1] = fma(m, u_n, isel(up_left, pL, pR) + pmul<EMU, true>(g, un - sc, ok));
 #pragma unroll
-  for (int t = 0; t < NT; ++t) G[2 + t] = fma(m, isel(up_left, utL[t], utR[t]), g * ut[t]);
-  G[E] = fma(u_n, isel(up_left, eL, eR), g * fma(-c, aun, H));
+  for (int t = 0; t < NT; ++t) G[2 + t] = fma(m, isel(up_left, utL[t], utR[t]), pmul<EMU, true>(g, ut[t], ok));
+  G[E] = fma(u_n, isel(up_left, eL, eR), pmul<EMU, true>(g, fma(-c, aun, H), ok));
+}
+
+// The Roe flux above with its products on the integer pipe; a warp in which
+// any lane's product left the integer path (a zero, subnormal, infinite or
+// NaN operand or result outside the cases pmul takes) evaluates it again in
+// FP64.  Both give the same bits wherever the integer path applies.
+template <int NT>
+__device__ __forceinline__ void roe_F(const double (&QL)[NT + 3], const double (&QR)[NT + 3], double g1,
+                                      double efix, double inv2efix, double (&G)[NT + 3]) {
+  bool ok = true;
+  roe_F_impl<NT, true>(QL, QR, g1, efix, inv2efix, G, ok);
+  if (__any_sync(__activemask(), !ok)) roe_F_impl<NT, false>(QL, QR, g1, efix, inv2efix, G, ok);
 }
 
 // ------------------------------------------------------------ mbarrier / TMA (inline PTX)

@@ -9,6 +9,10 @@ namespace fvk {
 
 // Largest CTA of the 3D box-tiled stage kernel (its register budget).
 constexpr int kStage3dMaxThreads = 192;
+// 2D stage kernels are built twice: for CTAs of up to this many threads (two
+// resident CTAs leave 170 registers per thread for the face runs and their
+// integer-pipe products) and for larger CTAs up to 256 (128 registers).
+constexpr int kStage2dMaxThreads = 192;
 // Largest CTA of the split kernels (FV_SPLIT; their register budget).
 constexpr int kSplitMaxThreads = 512;
 

@@ -13,18 +13,25 @@ size_t stage_smem_bytes(int dim, const int tile[3]) {
 }
 
 cudaError_t launch_stage_2d(int, const CUtensorMap *, const StageArgs &, int, cudaStream_t);
+cudaError_t launch_stage_2d_wide(int, const CUtensorMap *, const StageArgs &, int, cudaStream_t);
 cudaError_t launch_stage_3d(int, const CUtensorMap *, const StageArgs &, int, cudaStream_t);
 cudaError_t set_stage_attributes_2d(size_t);
+cudaError_t set_stage_attributes_2d_wide(size_t);
 cudaError_t set_stage_attributes_3d(size_t);
 
 cudaError_t launch_stage(int dim, int mode, const CUtensorMap *tmap, const StageArgs &a, int threads,
                          cudaStream_t st) {
-  if (dim == 2) return launch_stage_2d(mode, tmap, a, threads, st);
+  if (dim == 2)
+    return threads > kStage2dMaxThreads ? launch_stage_2d_wide(mode, tmap, a, threads, st)
+                                        : launch_stage_2d(mode, tmap, a, threads, st);
   return a.march ? launch_march(mode, tmap, a, threads, st) : launch_stage_3d(mode, tmap, a, threads, st);
 }
 
 cudaError_t stage_kernel_attributes(int dim, size_t smem) {
-  if (dim == 2) return set_stage_attributes_2d(smem);
+  if (dim == 2) {
+    const cudaError_t e = set_stage_attributes_2d(smem);
+    return e == cudaSuccess ? set_stage_attributes_2d_wide(smem) : e;
+  }
   const cudaError_t e = set_stage_attributes_3d(smem);
   return e == cudaSuccess ? set_march_attributes(smem) : e;
 }
@@ -230,6 +237,13 @@ __global__ void debug_bits_kernel(int op, const double *x, const double *y, doub
       case 2: r = scale_pow2<-1>(v); break;
       case 3: r = scale_pow2<1>(v); break;
       case 4: r = minmod(v, y[i]); break;
+      case 6:
+      case 7: {  // the flux kernels' products: on the integer path, else FP64
+        bool ok = true;
+        r = op == 6 ? pmul<true, false>(v, y[i], ok) : pmul<true, true>(v, y[i], ok);
+        if (!ok) r = v * y[i];
+        break;
+      }
       default: r = iabs(v); break;
     }
     out[i] = r;

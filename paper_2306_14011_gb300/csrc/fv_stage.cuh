@@ -468,15 +468,17 @@ __device__ __forceinline__ double *aligned_smem(unsigned char *raw) {
 }
 
 // One CTA per tile of the grid.  Register budget: FV_STAGE_MIN_BLOCKS resident
-// CTAs of the largest allowed size per SM (2 by default; the default tiles'
-// shared memory also allows two CTAs per SM).  2D CTAs have up to 256
-// threads (up to 128 registers per thread, no spills); 3D CTAs up to 192,
-// which leaves 168 registers for the five-variable face runs (256 would spill).
+// CTAs of MAXT threads per SM (2 by default; the default tiles' shared memory
+// also allows two CTAs per SM).  2D kernels come in two sizes: up to
+// kStage2dMaxThreads threads (170 registers per thread for the face runs and
+// their integer-pipe products) and up to 256 (128 registers); 3D box kernels
+// take up to kStage3dMaxThreads threads (168 registers: the five-variable
+// runs would spill at 128).
 #ifndef FV_STAGE_MIN_BLOCKS
 #define FV_STAGE_MIN_BLOCKS 2
 #endif
-template <int DIM, int MODE, int LIM>
-__global__ void __launch_bounds__(DIM == 2 ? 256 : kStage3dMaxThreads, FV_STAGE_MIN_BLOCKS)
+template <int DIM, int MODE, int LIM, int MAXT>
+__global__ void __launch_bounds__(MAXT, FV_STAGE_MIN_BLOCKS)
     stage_kernel(const __grid_constant__ CUtensorMap tmap, const StageArgs a) {
   constexpr int NV = DIM + 2;
   extern __shared__ unsigned char smem_raw[];
@@ -499,38 +501,38 @@ __global__ void __launch_bounds__(DIM == 2 ? 256 : kStage3dMaxThreads, FV_STAGE_
   tile_work<DIM, MODE, LIM>(&tmap, a, bx, by, bz, tile, mbar, 0u, s_coef, red);
 }
 
-template <int DIM, int LIM>
+template <int DIM, int LIM, int MAXT>
 cudaError_t launch_stage_lim(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st) {
   const size_t smem = stage_smem_bytes(DIM, a.tile);
   const long long nblk = a.tile_count > 0 ? a.tile_count : (long long)a.ntile[0] * a.ntile[1] * a.ntile[2] - a.tile_begin;
   const dim3 grid((unsigned)nblk), block(threads);
   switch (mode) {
-    case MODE_RESIDUAL: stage_kernel<DIM, MODE_RESIDUAL, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
-    case MODE_STAGE1: stage_kernel<DIM, MODE_STAGE1, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
-    case MODE_STAGE2: stage_kernel<DIM, MODE_STAGE2, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
-    default: stage_kernel<DIM, MODE_STAGE3, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_RESIDUAL: stage_kernel<DIM, MODE_RESIDUAL, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_STAGE1: stage_kernel<DIM, MODE_STAGE1, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_STAGE2: stage_kernel<DIM, MODE_STAGE2, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
+    default: stage_kernel<DIM, MODE_STAGE3, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
   }
   return cudaGetLastError();
 }
 
-template <int DIM>
+template <int DIM, int MAXT>
 cudaError_t launch_stage_dim(int mode, const CUtensorMap *tmap, const StageArgs &a, int threads, cudaStream_t st) {
-  if (a.limiter == FV_LIM_VANLEER) return launch_stage_lim<DIM, FV_LIM_VANLEER>(mode, tmap, a, threads, st);
-  if (a.limiter == FV_LIM_NONE) return launch_stage_lim<DIM, FV_LIM_NONE>(mode, tmap, a, threads, st);
-  return launch_stage_lim<DIM, FV_LIM_MINMOD>(mode, tmap, a, threads, st);
+  if (a.limiter == FV_LIM_VANLEER) return launch_stage_lim<DIM, FV_LIM_VANLEER, MAXT>(mode, tmap, a, threads, st);
+  if (a.limiter == FV_LIM_NONE) return launch_stage_lim<DIM, FV_LIM_NONE, MAXT>(mode, tmap, a, threads, st);
+  return launch_stage_lim<DIM, FV_LIM_MINMOD, MAXT>(mode, tmap, a, threads, st);
 }
 
 // Allow each stage kernel the largest dynamic shared memory the device offers
 // (opt-in limit minus the kernel's static shared memory), so contexts with
 // different tile shapes never lower each other's limit.  `smem_optin` is the
 // device's per-block opt-in limit.
-template <int DIM, int LIM>
+template <int DIM, int LIM, int MAXT>
 cudaError_t set_stage_attributes_lim(size_t smem_optin) {
   cudaError_t e = cudaSuccess;
-  const void *k[4] = {(const void *)stage_kernel<DIM, MODE_RESIDUAL, LIM>,
-                      (const void *)stage_kernel<DIM, MODE_STAGE1, LIM>,
-                      (const void *)stage_kernel<DIM, MODE_STAGE2, LIM>,
-                      (const void *)stage_kernel<DIM, MODE_STAGE3, LIM>};
+  const void *k[4] = {(const void *)stage_kernel<DIM, MODE_RESIDUAL, LIM, MAXT>,
+                      (const void *)stage_kernel<DIM, MODE_STAGE1, LIM, MAXT>,
+                      (const void *)stage_kernel<DIM, MODE_STAGE2, LIM, MAXT>,
+                      (const void *)stage_kernel<DIM, MODE_STAGE3, LIM, MAXT>};
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, k[i]);
@@ -541,11 +543,11 @@ cudaError_t set_stage_attributes_lim(size_t smem_optin) {
   return e;
 }
 
-template <int DIM>
+template <int DIM, int MAXT>
 cudaError_t set_stage_attributes_dim(size_t smem_optin) {
-  cudaError_t e = set_stage_attributes_lim<DIM, FV_LIM_MINMOD>(smem_optin);
-  if (e == cudaSuccess) e = set_stage_attributes_lim<DIM, FV_LIM_VANLEER>(smem_optin);
-  if (e == cudaSuccess) e = set_stage_attributes_lim<DIM, FV_LIM_NONE>(smem_optin);
+  cudaError_t e = set_stage_attributes_lim<DIM, FV_LIM_MINMOD, MAXT>(smem_optin);
+  if (e == cudaSuccess) e = set_stage_attributes_lim<DIM, FV_LIM_VANLEER, MAXT>(smem_optin);
+  if (e == cudaSuccess) e = set_stage_attributes_lim<DIM, FV_LIM_NONE, MAXT>(smem_optin);
   return e;
 }
 

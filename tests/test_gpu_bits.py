@@ -1,8 +1,9 @@
 """The kernels' integer-pipe replacements of FP64 operations, bit for bit.
 
-minmod, |x| and the exponent shifts (x/2, x/4, 2x) run on the integer pipe
-inside the stage, reduction and adjoint kernels; each is claimed to equal its
-FP64 definition exactly.  fv_debug_bits applies them on the GPU to special
+minmod, |x|, the exponent shifts (x/2, x/4, 2x) and the products of the flux
+(x * y on 32-bit integer operations) run on the integer pipe inside the stage,
+reduction and adjoint kernels; each is claimed to equal its FP64 definition
+exactly.  fv_debug_bits applies them on the GPU to special
 values (signed zeros, subnormals, the normal-range edges, infinities, NaN)
 and to random bit patterns across every exponent.
 """
@@ -79,3 +80,39 @@ def test_minmod_equals_its_definition_on_finite_values():
     assert np.all(got == exp)  # values (a zero result may be -0 only from a zero argument)
     nz = exp != 0
     assert np.array_equal(got[nz].view(np.uint64), exp[nz].view(np.uint64))
+
+
+def test_integer_pipe_product_equals_fp64_multiplication():
+    """pmul (the flux kernels' products on 32-bit integer operations) against
+    the FP64 multiplier: random bit patterns over every exponent, operand
+    pairs whose product lands near the ends of the normal range, short
+    significands (exact products and ties to even), significands that round
+    up into the next binade, and the special values (zeros, subnormals,
+    infinities, NaN) that take the FP64 path."""
+    rng = np.random.default_rng(11)
+    n = 1 << 20
+    x = _values(8, n)
+    y = np.concatenate([_values(9, n)[::-1][:x.size - 24], _values(9, 24)[:24]])
+    # ordinary magnitudes, as in the fluxes
+    a = rng.uniform(-4, 4, n) * 10.0 ** rng.integers(-8, 8, n)
+    b = rng.uniform(-4, 4, n) * 10.0 ** rng.integers(-8, 8, n)
+    # short significands: exact products and halfway cases
+    sa = np.ldexp(rng.integers(1 << 26, 1 << 27, n).astype(np.float64), rng.integers(-40, 40, n))
+    sb = np.ldexp(rng.integers(1 << 26, 1 << 27, n).astype(np.float64), rng.integers(-40, 40, n))
+    # products near the largest and the smallest normal double
+    ea = rng.integers(0, 1000, n)
+    top = np.ldexp(rng.uniform(1, 2, n), ea)
+    bot = np.ldexp(rng.uniform(1, 2, n), -ea)
+    hi = np.ldexp(rng.uniform(1, 2, n), 1023 - ea - rng.integers(0, 2, n))
+    lo = np.ldexp(rng.uniform(1, 2, n), -1022 + ea + rng.integers(-1, 2, n))
+    # significands of all ones times values just above 1 (rounding carries)
+    ones = np.ldexp(np.float64(2.0) - np.ldexp(1.0, -52) * rng.integers(0, 4, n), rng.integers(-20, 20, n))
+    up = 1.0 + np.ldexp(1.0, -52) * rng.integers(1, 64, n)
+    X = np.concatenate([x, a, sa, top, bot, ones])
+    Y = np.concatenate([y, b, sb, hi, lo, up])
+    with np.errstate(over="ignore", under="ignore", invalid="ignore"):
+        exp = X * Y
+    for op in (6, 7):  # without and with signed zeros on the integer path
+        got = _run(op, X, Y)
+        bad = ~_same_bits(got, exp)
+        assert not bad.any(), (op, X[bad][:5], Y[bad][:5], got[bad][:5], exp[bad][:5])

@@ -276,7 +276,7 @@ def test_launch_configuration_does_not_change_results(dim):
     if dim == 2:
         g, U = I.kelvin_helmholtz(160, seed=1)
         cfgs = [((32, 16, 1), 256), ((16, 8, 1), 64), ((64, 4, 1), 128), ((8, 32, 1), 96), ((2, 2, 1), 32),
-                ((128, 2, 1), 256)]
+                ((128, 2, 1), 192), ((64, 16, 1), 160), ((32, 8, 1), 224)]
     else:
         g, U = I.taylor_green(20, seed=2)
         cfgs = [((16, 8, 4), 192), ((8, 8, 8), 128), ((4, 4, 2), 32), ((20, 4, 2), 160)]

@@ -68,7 +68,7 @@ def test_launch_invariance():
     g, U = I.kelvin_helmholtz(96, seed=2)
     outs = []
     for tile, thr, loader in [((32, 32, 1), 160, fv.FV_LOADER_TMA), ((16, 8, 1), 64, fv.FV_LOADER_PLAIN),
-                              ((64, 4, 1), 256, fv.FV_LOADER_TMA)]:
+                              ((64, 4, 1), 192, fv.FV_LOADER_TMA)]:
         d = fv.launch_to_dict(fv.fv_default_launch(g))
         for st in range(3):
             d["stage"][st].update(tile=tile, threads=thr, loader=loader)

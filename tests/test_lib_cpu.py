@@ -44,7 +44,7 @@ def test_strerror_and_default_launch_without_gpu():
     assert fv.strerror(fv.FV_EINVAL) == "invalid argument"
     assert fv.strerror(99) == "unknown status"
     l2 = fv.fv_default_launch(I.grid2d(64, 64, 1.0, 1.0))
-    assert tuple(l2.stage[0].tile) == (32, 32, 1) and l2.stage[0].threads == 160
+    assert tuple(l2.stage[0].tile) == (64, 16, 1) and l2.stage[0].threads == 192
     assert l2.dt.threads == 512 and l2.dt.grid == 0
     l3 = fv.fv_default_launch(I.grid3d(16, 16, 16, 1.0, 1.0, 1.0))
     assert tuple(l3.stage[2].tile) == (8, 8, 8) and l3.stage[2].threads == 192 and l3.stage[2].march == 0
