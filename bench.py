@@ -66,11 +66,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # dram__bytes_write.sum, full 4096^2 launches, mean of the three stages of one
 # step), valid for the kernel sources whose hash and the launch shape recorded
 # with it; null otherwise.
-STAGE_TRAFFIC = {"bytes": 1.3894e9, "source_hash": "b4695b9080b1984a", "tile": [32, 32, 1], "threads": 160}
+STAGE_TRAFFIC = {"bytes": 1.3891e9, "source_hash": "2cc4ed5e8e87d8e4", "tile": [64, 16, 1], "threads": 192}
 # FP64 instructions the fused stage kernels execute per cell and stage (ncu
 # sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on, mean of the three
-# stages at 2048^2 / 192^3), for the kernel sources with this hash.
-STAGE_FP64_INST = {"2d": 190.9, "3d": 361.8, "source_hash": "b4695b9080b1984a"}
+# stages at 2048^2 / 192^3), for the kernel sources with this hash; and the
+# FP64 products evaluated on the integer pipe instead: 32 per face in 2D and 35
+# in 3D (the Roe flux's products), times the faces per cell of the default
+# tiles (2.078 for 64x16, 3.375 for 8x8x8).
+STAGE_FP64_INST = {"2d": 128.1, "3d": 247.1, "source_hash": "2cc4ed5e8e87d8e4"}
+INT_PIPE_PRODUCTS = {"2d": 66.5, "3d": 118.1}
 
 
 # The naive default launch of the tuning comparison: 32x8 threads, one cell
@@ -343,13 +347,18 @@ def run_ours(args):
         # the kernel's FP64 instruction rate against a DFMA stream kernel on
         # the same device and clock (the issue-rate ceiling in practice)
         stream_rate = fv.fv_debug_fp64_rate(0)
+        int_rate, mixed_rate = fv.fv_debug_fp64_rate(2), fv.fv_debug_fp64_rate(3)
         inst = STAGE_FP64_INST["2d" if g.dim == 2 else "3d"]
         if STAGE_FP64_INST["source_hash"] != kernel_source_hash():
             inst = None
         rate = inst * cells / (stage_ms / 1e3) if inst else None
+        key = "2d" if g.dim == 2 else "3d"
         line["roofline"]["fp64_stream"] = {
             "dfma_stream_lane_ops_per_s": stream_rate, "kernel_fp64_inst_per_cell_stage": inst,
-            "kernel_fp64_lane_ops_per_s": rate, "frac_of_stream": rate / stream_rate if rate else None}
+            "kernel_fp64_lane_ops_per_s": rate, "frac_of_stream": rate / stream_rate if rate else None,
+            "int_pipe_products_per_cell_stage": INT_PIPE_PRODUCTS[key] if inst else None,
+            "int_pipe_product_stream_ops_per_s": int_rate, "dfma_beside_int_products_stream_ops_per_s": mixed_rate,
+            "note": "FP64 pipe share of the work; the flux products run on the integer pipe beside it"}
     if args.workload != "kh4096":
         line["metric"] = W["metric"]
     if world == 1 and not W["batched"] and args.tune_samples > 0:

@@ -387,11 +387,13 @@ int fv_debug_math(const double *x, double *out_rsqrt, double *out_rcp, long n, v
 
 /* Reference FP64 issue rate of the current device (not in the paper; for
  * reporting the ALU roofline): a kernel of 8 x SMs CTAs of 256 threads, each
- * thread running 8 independent chains of 4096 DFMA (kind 0) or DADD (kind 1)
- * operations, timed with CUDA events on `stream` after a short warm-up.
- * *lane_ops_per_s receives FP64 operations (lanes) per second.  Allocates
- * and frees 256 doubles per CTA; synchronises `stream`.  FV_EINVAL for a bad
- * kind or a NULL output. */
+ * thread running 8 independent chains of 4096 operations -- kind 0: DFMA,
+ * kind 1: DADD, kind 2: the flux kernels' products on the integer pipe
+ * (bit for bit the FP64 product), kind 3: 4 DFMA chains beside 4 integer-pipe
+ * product chains -- timed with CUDA events on `stream` after a short
+ * warm-up.  *lane_ops_per_s receives operations (lanes) per second.
+ * Allocates and frees 256 doubles per CTA; synchronises `stream`.  FV_EINVAL
+ * for a bad kind or a NULL output. */
 int fv_debug_fp64_rate(int kind, double *lane_ops_per_s, void *stream);
 
 /* The kernels' integer-pipe replacements of FP64 operations, applied to n

@@ -1156,7 +1156,7 @@ int fv_debug_bits(int op, const double *x, const double *y, double *out, long n,
 }
 
 int fv_debug_fp64_rate(int kind, double *lane_ops_per_s, void *stream) {
-  if ((kind != 0 && kind != 1) || !lane_ops_per_s) return FV_EINVAL;
+  if (kind < 0 || kind > 3 || !lane_ops_per_s) return FV_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int dev = 0, sms = 0;
   FV_CK(cudaGetDevice(&dev));

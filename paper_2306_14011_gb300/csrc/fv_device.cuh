@@ -135,14 +135,28 @@ __device__ __forceinline__ double rcp_seed(double x) {
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
   return y;
 }
+// The same seeds as volatile asm, for the FP64 re-evaluation of the flux in
+// a rarely taken branch: the compiler can then neither share them with the
+// integer-path evaluation nor hoist the products that depend on them above
+// the branch (where they would run on every call).
+__device__ __forceinline__ double rsqrt_seed_v(double x) {
+  double y;
+  asm volatile("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+__device__ __forceinline__ double rcp_seed_v(double x) {
+  double y;
+  asm volatile("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
 
 // 1/sqrt(x) for positive normal x.  With y0 the seed and e = 1 - x*y0^2,
 // 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)); truncating
 // the binomial series after e^2 is the third-order Householder step, so
 // |e| < 2^-20 leaves a truncation error below 2^-59 (5 FP64 operations).
-template <bool EMU = false>
+template <bool EMU = false, bool VOLATILE_SEED = false>
 __device__ __forceinline__ double rsqrt_fp64(double x, bool &ok) {
-  const double y = rsqrt_seed(x);
+  const double y = VOLATILE_SEED ? rsqrt_seed_v(x) : rsqrt_seed(x);
   const double t = pmul<EMU>(x, y, ok);
   const double e = fma(-t, y, 1.0);
   const double c = fma(e, 0.375, 0.5);
@@ -156,8 +170,9 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {
 
 // 1/x for normal x: 1/x = y0 / (1 - e) with e = 1 - x*y0, so
 // 1/x = y0 (1 + e + e^2 + O(e^3)) (3 FP64 operations, same truncation order).
+template <bool VOLATILE_SEED = false>
 __device__ __forceinline__ double rcp_fp64(double x) {
-  const double y = rcp_seed(x);
+  const double y = VOLATILE_SEED ? rcp_seed_v(x) : rcp_seed(x);
   const double e = fma(-x, y, 1.0);
   const double ee = fma(e, e, e);
   return fma(y, ee, y);
@@ -269,7 +284,7 @@ __device__ __forceinline__ void roe_F_impl(const double (&QL)[NT + 3], const dou
                                            double efix, double inv2efix, double (&G)[NT + 3], bool &ok) {
   constexpr int E = NT + 2;
   // left primitives: 1/sqrt(rho) gives both sqrt(rho) and 1/rho
-  const double tL = rsqrt_fp64<EMU>(QL[0], ok);
+  const double tL = rsqrt_fp64<EMU, !EMU>(QL[0], ok);
   const double rL = pmul<EMU>(tL, tL, ok);
   const double sL = pmul<EMU>(QL[0], tL, ok);
   const double unL = pmul<EMU, true>(QL[1], rL, ok);
@@ -283,7 +298,7 @@ __device__ __forceinline__ void roe_F_impl(const double (&QL)[NT + 3], const dou
   const double pL = pmul<EMU>(g1, fma(-0.5, kL, QL[E]), ok);
   const double eL = QL[E] + pL;  // rho h_t
   // right primitives
-  const double tR = rsqrt_fp64<EMU>(QR[0], ok);
+  const double tR = rsqrt_fp64<EMU, !EMU>(QR[0], ok);
   const double rR = pmul<EMU>(tR, tR, ok);
   const double sR = pmul<EMU>(QR[0], tR, ok);
   const double unR = pmul<EMU, true>(QR[1], rR, ok);
@@ -300,7 +315,7 @@ __device__ __forceinline__ void roe_F_impl(const double (&QL)[NT + 3], const dou
   // Roe averages with sqrt(rho) weights wL = sL / (sL + sR), wR = 1 - wL:
   // u~ = uR - wL (uR - uL), and H~ = (sL HL + sR HR) / (sL + sR) with
   // sL HL = eL / sL = eL tL
-  const double inv = rcp_fp64(sL + sR);
+  const double inv = rcp_fp64<!EMU>(sL + sR);
   const double wL = pmul<EMU>(sL, inv, ok);
   const double dun = unR - unL;
   const double un = fma(-wL, dun, unR);
@@ -314,7 +329,7 @@ __device__ __forceinline__ void roe_F_impl(const double (&QL)[NT + 3], const dou
   const double H = pmul<EMU>(fma(eL, tL, pmul<EMU>(eR, tR, ok)), inv, ok);
   const double rho = pmul<EMU>(sL, sR, ok);
   const double c2 = pmul<EMU>(g1, H - half_nonneg(q2), ok);
-  const double tc = rsqrt_fp64<EMU>(c2, ok);  // 1/c~
+  const double tc = rsqrt_fp64<EMU, !EMU>(c2, ok);  // 1/c~
   const double c = pmul<EMU>(c2, tc, ok);
 
   // the acoustic wave that crosses from downwind (upper signs: u~_n >= 0)

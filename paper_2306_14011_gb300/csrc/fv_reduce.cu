@@ -259,24 +259,46 @@ cudaError_t launch_debug_bits(int op, const double *x, const double *y, double *
 }
 
 // FP64 issue-rate reference: every thread runs 8 independent chains of
-// `iters` DFMA (kind 0) or DADD (kind 1) operations; out receives one sum
-// per thread so nothing is optimised away.
-__global__ void __launch_bounds__(256) fp64_stream_kernel(int kind, double a, double b, int iters, double *out) {
+// `iters` operations -- kind 0: DFMA, kind 1: DADD, kind 2: products on the
+// integer pipe (pmul, the flux kernels' products), kind 3: 4 DFMA chains
+// beside 4 integer-pipe product chains -- and out receives one sum per
+// thread so nothing is optimised away (NaN if a product left the integer
+// path, which the factors near 1 never make it do).
+template <int KIND>
+__global__ void __launch_bounds__(256) fp64_stream_kernel(double a, double b, int iters, double *out) {
   double x[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) x[i] = a + threadIdx.x * 1e-9 + i;
+  bool ok = true;
+  // factors just above and below 1 (alternating, selected on the integer
+  // pipe), so that product chains stay near their start
+  const long long up = __double_as_longlong(1.0000000001234), down = __double_as_longlong(0.9999999998766);
   for (int it = 0; it < iters; ++it) {
+    const double f = __longlong_as_double((it & 1) ? down : up);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) x[i] = kind == 0 ? fma(x[i], a, b) : x[i] + b;
+    for (int i = 0; i < 8; ++i) {
+      if (KIND == 0 || (KIND == 3 && i < 4))
+        x[i] = fma(x[i], a, b);
+      else if (KIND == 1)
+        x[i] = x[i] + b;
+      else
+        x[i] = pmul<true>(x[i], f, ok);
+    }
   }
   double s = 0.0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) s += x[i];
-  out[(long)blockIdx.x * blockDim.x + threadIdx.x] = s;
+  out[(long)blockIdx.x * blockDim.x + threadIdx.x] = ok ? s : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 cudaError_t launch_fp64_stream(int kind, int blocks, int iters, double *out, cudaStream_t st) {
-  fp64_stream_kernel<<<blocks, 256, 0, st>>>(kind, 1.0000001, 1e-7, iters, out);
+  const double a = 1.0000001, b = 1e-7;
+  switch (kind) {
+    case 0: fp64_stream_kernel<0><<<blocks, 256, 0, st>>>(a, b, iters, out); break;
+    case 1: fp64_stream_kernel<1><<<blocks, 256, 0, st>>>(a, b, iters, out); break;
+    case 2: fp64_stream_kernel<2><<<blocks, 256, 0, st>>>(a, b, iters, out); break;
+    default: fp64_stream_kernel<3><<<blocks, 256, 0, st>>>(a, b, iters, out); break;
+  }
   return cudaGetLastError();
 }
 

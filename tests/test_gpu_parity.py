@@ -323,7 +323,8 @@ def test_fp64_stream_rate_is_below_the_unit_count_peak():
     """The reference FP64 issue rate (DFMA and DADD streams) is positive and at
     most 2 lanes per clock per SM at the device's maximum clock (measured
     near 84% of it at full clock; the lower bound only rules out a broken
-    measurement, since a shared GPU may run at a lower clock)."""
+    measurement, since a shared GPU may run at a lower clock); DFMA chains
+    beside integer-pipe product chains together exceed that FP64 bound."""
     props = torch.cuda.get_device_properties(0)
     sms = props.multi_processor_count
     clk_hz = 2.07e9 if "GB300" in props.name else None
@@ -332,6 +333,13 @@ def test_fp64_stream_rate_is_below_the_unit_count_peak():
         assert r > 0
         if clk_hz:
             assert 0.25 <= r / (2 * sms * clk_hz) <= 1.0, r
+    # products on the integer pipe: measured near the DFMA stream's rate alone
+    # and, beside DFMA chains, above what the FP64 pipe alone can issue
+    emu = fv.fv_debug_fp64_rate(2)
+    mixed = fv.fv_debug_fp64_rate(3)
+    assert emu > 0 and mixed > 0
+    if clk_hz:
+        assert mixed > 2 * sms * clk_hz, mixed
 
 
 def test_refined_rsqrt_and_reciprocal_are_within_two_ulp():

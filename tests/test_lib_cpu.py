@@ -107,7 +107,8 @@ def test_tuning_space_sizes():
 
 def test_fp64_rate_rejects_bad_arguments_on_the_host():
     lib = fv.load()
-    assert lib.fv_debug_fp64_rate(2, C.byref(C.c_double()), None) == fv.FV_EINVAL
+    assert lib.fv_debug_fp64_rate(4, C.byref(C.c_double()), None) == fv.FV_EINVAL
+    assert lib.fv_debug_fp64_rate(-1, C.byref(C.c_double()), None) == fv.FV_EINVAL
     assert lib.fv_debug_fp64_rate(0, None, None) == fv.FV_EINVAL
 
 
