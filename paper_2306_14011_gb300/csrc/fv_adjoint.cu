@@ -218,11 +218,12 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
   __syncthreads();
 }
 
-// Register budget: two 256-thread CTAs per SM in 2D; in 3D the 8x4x4 tile's
-// shared memory (128 KB) allows one CTA per SM anyway, so the kernel may use
-// the whole register file (the five-variable reverse pass would spill at 128).
+// Register budget: two CTAs of kAdjThreads2d threads per SM in 2D (170
+// registers per thread for the reverse pass and its integer-pipe products);
+// in 3D the 8x4x4 tile's shared memory (128 KB) allows one CTA per SM
+// anyway, so the kernel may use the whole register file.
 template <int DIM>
-__global__ void __launch_bounds__(256, DIM == 2 ? 2 : 1) adjoint_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(DIM == 2 ? kAdjThreads2d : 256, DIM == 2 ? 2 : 1) adjoint_kernel(const AdjArgs a) {
   constexpr int NV = DIM + 2;
   extern __shared__ unsigned char smem_raw[];
   double *Ubox = aligned_smem(smem_raw);

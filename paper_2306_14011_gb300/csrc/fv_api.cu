@@ -1069,7 +1069,7 @@ int adjoint(fv_ctx *c, const double *U, const double *lam, double *out, double w
   a.half_eps = 0.5 * c->scheme.eps;
   a.efix = c->scheme.efix;
   a.inv2efix = c->scheme.efix > 0.0 ? 0.5 / c->scheme.efix : 0.0;
-  FV_CK(launch_adjoint(g.dim, a, 256, c->stream));
+  FV_CK(launch_adjoint(g.dim, a, g.dim == 2 ? kAdjThreads2d : 256, c->stream));
   return FV_OK;
 }
 

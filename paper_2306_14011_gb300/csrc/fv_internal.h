@@ -13,6 +13,8 @@ constexpr int kStage3dMaxThreads = 192;
 // resident CTAs leave 170 registers per thread for the face runs and their
 // integer-pipe products) and for larger CTAs up to 256 (128 registers).
 constexpr int kStage2dMaxThreads = 192;
+// CTA size of the 2D adjoint kernel (the 3D one takes 256).
+constexpr int kAdjThreads2d = 192;
 // Largest CTA of the split kernels (FV_SPLIT; their register budget).
 constexpr int kSplitMaxThreads = 512;
 
