@@ -150,18 +150,28 @@ __device__ __forceinline__ double rcp_seed_v(double x) {
   return y;
 }
 
+// The second-order series term w = 2^-k e + c e^2 of a refinement
+// (emu_series2_bits: integer and FP32 operations, no FP64 instruction).
+template <int K>
+__device__ __forceinline__ double series2(double e, float c) {
+  uint32_t hw, lw;
+  emu_series2_bits((uint32_t)__double2hiint(e), (uint32_t)__double2loint(e), (uint32_t)K, c, hw, lw);
+  return __hiloint2double((int)hw, (int)lw);
+}
+
 // 1/sqrt(x) for positive normal x.  With y0 the seed and e = 1 - x*y0^2,
 // 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + O(e^3)); truncating
 // the binomial series after e^2 is the third-order Householder step, so
-// |e| < 2^-20 leaves a truncation error below 2^-59 (5 FP64 operations).
+// |e| < 2^-20 leaves a truncation error below 2^-59.  x*y0 is a product
+// (integer pipe with EMU), e an FMA, the series term w = e/2 + 3e^2/8 is
+// formed on the integer pipe (series2), and y0 (1 + w) one more FMA: two
+// FP64 instructions.
 template <bool EMU = false, bool VOLATILE_SEED = false>
 __device__ __forceinline__ double rsqrt_fp64(double x, bool &ok) {
   const double y = VOLATILE_SEED ? rsqrt_seed_v(x) : rsqrt_seed(x);
   const double t = pmul<EMU>(x, y, ok);
   const double e = fma(-t, y, 1.0);
-  const double c = fma(e, 0.375, 0.5);
-  const double ye = pmul<EMU, true>(y, e, ok);  // e is exactly 0 for an exact seed
-  return fma(ye, c, y);
+  return fma(y, series2<1>(e, 0.375f), y);
 }
 __device__ __forceinline__ double rsqrt_fp64(double x) {
   bool ok = true;
@@ -169,13 +179,13 @@ __device__ __forceinline__ double rsqrt_fp64(double x) {
 }
 
 // 1/x for normal x: 1/x = y0 / (1 - e) with e = 1 - x*y0, so
-// 1/x = y0 (1 + e + e^2 + O(e^3)) (3 FP64 operations, same truncation order).
+// 1/x = y0 (1 + e + e^2 + O(e^3)): e an FMA, w = e + e^2 on the integer
+// pipe, y0 (1 + w) an FMA (same truncation order).
 template <bool VOLATILE_SEED = false>
 __device__ __forceinline__ double rcp_fp64(double x) {
   const double y = VOLATILE_SEED ? rcp_seed_v(x) : rcp_seed(x);
   const double e = fma(-x, y, 1.0);
-  const double ee = fma(e, e, e);
-  return fma(y, ee, y);
+  return fma(y, series2<0>(e, 1.0f), y);
 }
 
 // van Leer's limited slope, 2ab / (a + b) when a and b share one strict sign,

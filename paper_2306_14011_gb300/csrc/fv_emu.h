@@ -102,4 +102,69 @@ FV_EMU_HD bool emu_dmul_bits_z(uint32_t ha, uint32_t la, uint32_t hb, uint32_t l
   return zero ? finite : ok;
 }
 
+// The second-order series term of the reciprocal and reciprocal square-root
+// refinements: w = 2^-k e + c e^2 (k = 0 or 1, c > 0 an FP32 constant), as
+// the bits of a double, for the small residual e = 1 - x y^n of a seed y
+// (1/x = y (1 + e + e^2 + ...), 1/sqrt(x) = y (1 + e/2 + 3 e^2/8 + ...)).
+// 2^-k e is exact (an exponent decrement); c e^2 is formed in FP32 (e
+// truncated to FP32: relative error below 2^-21) and added to it as an
+// integer number of its units in the last place, so w carries an absolute
+// error below 2^-21 c e^2 + one unit in the last place of w -- below 2^-60
+// for |e| < 2^-19, far below the rounding of the refined result y (1 + w).
+// Binade crossings of the addition are handled exactly; |e| below 2^-959
+// gives w = 0.  The same integer steps on the host and the GPU, so the FP64
+// and integer-pipe evaluations of the flux that use it agree bit for bit.
+FV_EMU_HD float emu_f32_from_bits(uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  __builtin_memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+FV_EMU_HD uint32_t emu_bits_from_f32(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  uint32_t b;
+  __builtin_memcpy(&b, &f, 4);
+  return b;
+#endif
+}
+FV_EMU_HD float emu_fmul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+
+FV_EMU_HD void emu_series2_bits(uint32_t he, uint32_t le, uint32_t k, float c, uint32_t &hw, uint32_t &lw) {
+  const uint32_t Ee = (he >> 20) & 0x7ffu;
+  const uint32_t neg = he & 0x80000000u;
+  const uint32_t Eb = Ee - k;                                  // exponent field of 2^-k e
+  const uint64_t f = ((uint64_t)(he & 0xfffffu) << 32) | le;  // its 52-bit fraction
+  // e^2 c in FP32 from e truncated to FP32 (|e| < 2^-126 makes it 0)
+  const uint32_t e32b = Ee > 896u ? (((Ee - 896u) << 23) | ((he & 0xfffffu) << 3) | (le >> 29)) : 0u;
+  const float e32 = emu_f32_from_bits(e32b);
+  const uint32_t qb = emu_bits_from_f32(emu_fmul_rn(emu_fmul_rn(c, e32), e32));
+  const uint32_t Eq = qb >> 23;                                // q >= 0
+  const uint64_t mq = Eq != 0u ? (uint64_t)((qb & 0x7fffffu) | 0x800000u) : 0u;
+  // K = q / ulp(2^-k e) = mq 2^(Eq - 150 - (Eb - 1075))
+  const int sh = (int)Eq + 925 - (int)Eb;
+  const uint64_t K = sh >= 0 ? (sh < 40 ? mq << sh : 0xffffffffffull) : (-sh < 32 ? mq >> (-sh) : 0ull);
+  const uint64_t one = 1ull << 52;
+  uint64_t bits;
+  if (!neg) {  // |w| = |2^-k e| + K
+    const uint64_t S = f + K;
+    bits = S < one ? (((uint64_t)Eb << 52) | S) : (((uint64_t)(Eb + 1u) << 52) | ((S - one) >> 1));
+  } else {     // |w| = |2^-k e| - K, into the binade below when K > f
+    bits = f >= K ? (((uint64_t)Eb << 52) | (f - K)) : (((uint64_t)(Eb - 1u) << 52) | (one - 2u * (K - f)));
+  }
+  const bool tiny = Ee < 64u;
+  hw = tiny ? 0u : ((uint32_t)(bits >> 32) | neg);
+  lw = tiny ? 0u : (uint32_t)bits;
+}
+
 }  // namespace fvk
