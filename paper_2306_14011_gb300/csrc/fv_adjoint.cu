@@ -77,7 +77,9 @@ __device__ void load_box(double *dst, const double *src, const AdjArgs &a, const
 // Faces along axis D: per face the cotangents sent to its four stencil cells
 // (c0..c3 for cells f-2 .. f+1), stored as 4*NV doubles; then every tile cell
 // gathers and accumulates scale * (sum) into acc.
-template <int DIM, int D>
+// HALF: the MUSCL factor eps/2 is 1/2 (eps = 1), so h * x is an exponent
+// decrement on the integer pipe (scale_pow2) instead of an FP64 product.
+template <int DIM, int D, bool HALF>
 __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb, double *acc, const AdjArgs &a,
                               const int o[3], const int ext[3], const AdjGeom &G, double scale) {
   constexpr int NV = DIM + 2;
@@ -161,7 +163,8 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
     // sign flips run on the integer pipe (isel, mul_sign), only the sums in FP64.
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const double hl = h * QLb[v], hr = h * QRb[v];
+      const double hl = HALF ? scale_pow2<-1>(QLb[v]) : h * QLb[v];
+      const double hr = HALF ? scale_pow2<-1>(QRb[v]) : h * QRb[v];
       const double nhl = mul_sign(hl, -1.0), nhr = mul_sign(hr, -1.0);
       const double c0 = isel(pL[v] == 1, nhl, 0.0);
       const double c3 = isel(pR[v] == 2, nhr, 0.0);
@@ -222,7 +225,7 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
 // registers per thread for the reverse pass and its integer-pipe products);
 // in 3D the 8x4x4 tile's shared memory (128 KB) allows one CTA per SM
 // anyway, so the kernel may use the whole register file.
-template <int DIM>
+template <int DIM, bool HALF>
 __global__ void __launch_bounds__(DIM == 2 ? kAdjThreads2d : 256, DIM == 2 ? 2 : 1) adjoint_kernel(const AdjArgs a) {
   constexpr int NV = DIM + 2;
   extern __shared__ unsigned char smem_raw[];
@@ -244,9 +247,9 @@ __global__ void __launch_bounds__(DIM == 2 ? kAdjThreads2d : 256, DIM == 2 ? 2 :
   load_box<DIM>(Ubox, a.U, a, o, ext, 3, G.UX, G.UY, G.uplane, false);
   load_box<DIM>(Lbox, a.lam, a, o, ext, 2, G.LX, G.LY, G.lplane, true);
   __syncthreads();
-  adj_face_pass<DIM, 0>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[0]);
-  adj_face_pass<DIM, 1>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[1]);
-  if constexpr (DIM == 3) adj_face_pass<DIM, 2>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[2]);
+  adj_face_pass<DIM, 0, HALF>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[0]);
+  adj_face_pass<DIM, 1, HALF>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[1]);
+  if constexpr (DIM == 3) adj_face_pass<DIM, 2, HALF>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[2]);
   const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
   const int ncell = ext[0] * ext[1] * ext[2];
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
@@ -271,18 +274,23 @@ size_t adjoint_smem_bytes(int dim, const int tile[3]) {
   return 128 + sizeof(double) * (size_t)nv * (G.uplane + G.lplane + 4 * G.fmax + G.cells);
 }
 
+template <int DIM, bool HALF>
+cudaError_t launch_adjoint_kernel(const AdjArgs &a, unsigned blocks, int threads, size_t smem, cudaStream_t st) {
+  const cudaError_t e = cudaFuncSetAttribute((const void *)adjoint_kernel<DIM, HALF>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) adjoint_kernel<DIM, HALF><<<blocks, threads, smem, st>>>(a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 cudaError_t launch_adjoint(int dim, const AdjArgs &a, int threads, cudaStream_t st) {
   const size_t smem = adjoint_smem_bytes(dim, a.tile);
   const unsigned blocks = (unsigned)((long long)a.ntile[0] * a.ntile[1] * a.ntile[2]);
-  cudaError_t e;
-  if (dim == 2) {
-    e = cudaFuncSetAttribute((const void *)adjoint_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) adjoint_kernel<2><<<blocks, threads, smem, st>>>(a);
-  } else {
-    e = cudaFuncSetAttribute((const void *)adjoint_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) adjoint_kernel<3><<<blocks, threads, smem, st>>>(a);
-  }
-  return e != cudaSuccess ? e : cudaGetLastError();
+  const bool half = a.half_eps == 0.5;
+  if (dim == 2)
+    return half ? launch_adjoint_kernel<2, true>(a, blocks, threads, smem, st)
+                : launch_adjoint_kernel<2, false>(a, blocks, threads, smem, st);
+  return half ? launch_adjoint_kernel<3, true>(a, blocks, threads, smem, st)
+              : launch_adjoint_kernel<3, false>(a, blocks, threads, smem, st);
 }
 
 }  // namespace fvk
