@@ -21,7 +21,9 @@
 // Per cell the face work is (1 + 1/tile[0]) + (1 + 1/tile[1]) + (1 + 1/tile[2])
 // fluxes (3.16 at 16 x 16 columns and 32-plane chunks) against 3.375 for an
 // 8 x 8 x 8 box tile, whose depth shared memory bounds; in exchange the CTA
-// synchronises twice per plane.  Two 256-thread CTAs fit on an SM.
+// synchronises twice per plane.  Two 256-thread CTAs fit on an SM.  Stages 2
+// and 3 copy U^n of each plane's columns into shared memory asynchronously
+// while the plane's faces are evaluated.
 #include "fv_stage.cuh"
 
 namespace fvk {
@@ -197,7 +199,8 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
   double *Fy = Fx + NV3 * G.nfx;
   double *Fz0 = Fy + NV3 * G.nfy;
   double *Fz1 = Fz0 + NV3 * G.cols;
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(Fz1 + NV3 * G.cols);
+  double *Unb = Fz1 + NV3 * G.cols;  // stages 2 and 3: U^n of the current plane's columns
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(Unb + NV3 * G.cols);
 
   const long long tix = a.tile_begin + blockIdx.x;  // linear tile index
   long long b = tix;
@@ -253,6 +256,17 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
   for (int k = 0; k < nzc; ++k) {
     const int r = k + 2;  // ring index of the current plane z0 + k
     double *cur = ring + (r & 3) * G.slot;
+    // stages 2 and 3: U^n of this plane's columns into Unb with asynchronous
+    // copies, issued by the thread that reads them in E, so their latency
+    // hides behind the plane's face work (E of the previous plane, the only
+    // reader of these entries, came before in this thread's program order)
+    if (MODE == MODE_STAGE2 || MODE == MODE_STAGE3)
+      for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        const int i = c % ext0, j = c / ext0;
+        const long long gi = ((long long)(z0 + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
+#pragma unroll
+        for (int v = 0; v < NV3; ++v) cp_async8(smem_u32(Unb + v * G.cols + c), a.Un + v * N + gi);
+      }
     // A. wait for plane r+2; patch the current plane's x-y halo
     ok = wait_plane(mbar, r + 2, a);
     if (a.use_tma) fix_plane_halo(cur, a, o, ext0, ext1, z0 + k, G);
@@ -280,6 +294,7 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
     }
     __syncthreads();
     // E. residual of the current plane and the epilogue
+    if (MODE == MODE_STAGE2 || MODE == MODE_STAGE3) cp_async_wait_all();  // this thread's U^n copies
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
       const int i = c % ext0, j = c / ext0;
       const int fx = j * zsx + i, fy = j * ext0 + i;
@@ -289,7 +304,7 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const __grid_constant__ C
       for (int v = 0; v < NV3; ++v) {
         // same accumulation as the box-tiled kernel: the stage base, then x, y, z
         const double dFx = Fx[v * G.nfx + fx + 1] - Fx[v * G.nfx + fx];
-        const double un = (MODE == MODE_STAGE2 || MODE == MODE_STAGE3) ? a.Un[v * N + gi] : 0.0;
+        const double un = (MODE == MODE_STAGE2 || MODE == MODE_STAGE3) ? Unb[v * G.cols + c] : 0.0;
         double rv = (MODE == MODE_RESIDUAL && !a.S)
                         ? cx * dFx
                         : fma(cx, dFx, start_value<MODE>(a, cur[v * G.plane + lc], un, v * N + gi, src));
@@ -356,7 +371,7 @@ cudaError_t set_march_attributes_lim(size_t smem_optin) {
 
 size_t march_smem_bytes(const int tile[3]) {
   const MarchGeom G = march_geom(tile);
-  return 128 + sizeof(double) * ((size_t)kRing * G.slot + (size_t)NV3 * (G.nfx + G.nfy + 2 * G.cols)) +
+  return 128 + sizeof(double) * ((size_t)kRing * G.slot + (size_t)NV3 * (G.nfx + G.nfy + 3 * G.cols)) +
          sizeof(uint64_t) * kRing;
 }
 
