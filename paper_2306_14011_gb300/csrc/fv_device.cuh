@@ -31,6 +31,12 @@ enum : unsigned { FLAG_NONPHYSICAL = 1u, FLAG_TIMEOUT = 2u };
 // ------------------------------------------------------------ integer-pipe helpers
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
+// The FP64 product for the rare inputs the integer-pipe replacements below
+// leave to the FP64 multiplier.  Kept out of line: a multiply written inside
+// their warp-uniform branches was speculated above the branch by the compiler
+// and then occupied the FP64 pipe on every call.
+static __device__ __noinline__ double dmul_fp64_slow(double a, double b) { return __dmul_rn(a, b); }
+
 // |x| by clearing the sign bit.
 __device__ __forceinline__ double iabs(double x) {
   return __hiloint2double(__double2hiint(x) & 0x7fffffff, __double2loint(x));
@@ -77,7 +83,9 @@ __device__ __forceinline__ double half_nonneg(double x) {
   const bool normal = b >= (2ll << 52) && b < 0x7ff0000000000000ll;
   const bool tiny = b > 0 && b < (2ll << 52);
   double h = __longlong_as_double(normal ? b - (1ll << 52) : (b <= 0 ? 0ll : b));
-  if (__any_sync(__activemask(), tiny)) h = isel(tiny, 0.5 * x, h);
+  if (__any_sync(__activemask(), tiny)) {
+    if (tiny) h = dmul_fp64_slow(0.5, x);
+  }
   return h;
 }
 
@@ -94,8 +102,7 @@ __device__ __forceinline__ double scale_pow2(double x) {
   const bool zero = izero(x);
   double q = __hiloint2double(fast ? hi + K * (1 << 20) : hi, __double2loint(x));
   if (__any_sync(__activemask(), !fast && !zero)) {
-    const double f = K == -2 ? 0.25 : (K == -1 ? 0.5 : 2.0);
-    q = isel(!fast && !zero, f * x, q);
+    if (!fast && !zero) q = dmul_fp64_slow(K == -2 ? 0.25 : (K == -1 ? 0.5 : 2.0), x);
   }
   return q;
 }
