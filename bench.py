@@ -66,15 +66,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # dram__bytes_write.sum, full 4096^2 launches, mean of the three stages of one
 # step), valid for the kernel sources whose hash and the launch shape recorded
 # with it; null otherwise.
-STAGE_TRAFFIC = {"bytes": 1.3891e9, "source_hash": "2cc4ed5e8e87d8e4", "tile": [64, 16, 1], "threads": 192}
+STAGE_TRAFFIC = {"bytes": 1.3893e9, "source_hash": "6bc4056cc9b5ba98", "tile": [64, 16, 1], "threads": 192}
 # FP64 instructions the fused stage kernels execute per cell and stage (ncu
 # sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on, mean of the three
 # stages at 2048^2 / 192^3), for the kernel sources with this hash; and the
-# FP64 products evaluated on the integer pipe instead: 32 per face in 2D and 35
+# FP64 products evaluated on the integer pipe instead: 29 per face in 2D and 32
 # in 3D (the Roe flux's products), times the faces per cell of the default
 # tiles (2.078 for 64x16, 3.375 for 8x8x8).
-STAGE_FP64_INST = {"2d": 128.1, "3d": 247.1, "source_hash": "2cc4ed5e8e87d8e4"}
-INT_PIPE_PRODUCTS = {"2d": 66.5, "3d": 118.1}
+STAGE_FP64_INST = {"2d": 114.3, "3d": 231.2, "source_hash": "6bc4056cc9b5ba98"}
+INT_PIPE_PRODUCTS = {"2d": 60.3, "3d": 108.0}
 
 
 # The naive default launch of the tuning comparison: 32x8 threads, one cell
