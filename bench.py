@@ -353,11 +353,17 @@ def run_ours(args):
             inst = None
         rate = inst * cells / (stage_ms / 1e3) if inst else None
         key = "2d" if g.dim == 2 else "3d"
+        prod = INT_PIPE_PRODUCTS[key] * cells / (stage_ms / 1e3) if inst else None
         line["roofline"]["fp64_stream"] = {
             "dfma_stream_lane_ops_per_s": stream_rate, "kernel_fp64_inst_per_cell_stage": inst,
             "kernel_fp64_lane_ops_per_s": rate, "frac_of_stream": rate / stream_rate if rate else None,
             "int_pipe_products_per_cell_stage": INT_PIPE_PRODUCTS[key] if inst else None,
+            "kernel_int_pipe_products_per_s": prod,
             "int_pipe_product_stream_ops_per_s": int_rate, "dfma_beside_int_products_stream_ops_per_s": mixed_rate,
+            # the kernels' FP64 instructions plus their integer-pipe products
+            # per second, against DFMA chains beside integer-pipe product
+            # chains: the ceiling of the two pipes working together
+            "combined_frac_of_mixed_stream": (rate + prod) / mixed_rate if rate else None,
             "note": "FP64 pipe share of the work; the flux products run on the integer pipe beside it"}
     if args.workload != "kh4096":
         line["metric"] = W["metric"]
