@@ -368,7 +368,7 @@ int fv_tune_space(int dim, int mode, int *n_params, double *size);
  * library's device image -- every GPU that loads libfv holds it until the
  * process exits -- holding nvar partial sums per tile.  With rnorm2 != NULL
  * the grid may have at most 131072 / nvar default tiles (2D: 32768 tiles of
- * 32x32 cells, e.g. 5792 x 5792; 3D: 26214 tiles of 8x8x8 cells); larger
+ * 64x16 cells, e.g. 5760 x 5760; 3D: 26214 tiles of 8x8x8 cells); larger
  * grids return FV_EINVAL before anything is launched.  The first call on each
  * device looks up the scratch array's device address (cudaGetSymbolAddress)
  * and sets kernel attributes: make that first call before any stream capture.

@@ -70,7 +70,7 @@ def test_noalloc_residual_allocates_nothing_after_first_use():
 
 def test_noalloc_residual_rejects_oversized_grids_and_host_pointers():
     sch = fv.make_scheme()
-    g = I.grid2d(5792, 5824, 1.0, 1.0)  # 181 x 182 = 32942 tiles of 32x32: above the 32768 of the scratch
+    g = I.grid2d(5792, 5824, 1.0, 1.0)  # 91 x 364 = 33124 default tiles of 64x16: above the 32768 of the scratch
     U = torch.empty(g.shape, dtype=torch.float64, device="cuda")
     R = torch.empty_like(U)
     nrm = torch.zeros(g.nvar, dtype=torch.float64, device="cuda")
