@@ -92,6 +92,7 @@ struct GraphEntry {
   long long dt_bits;  // fixed dt bits, or 0 for CFL steps
   int steps;
   cudaGraphExec_t exec;
+  void *aux = nullptr;  // device memory the graph reads (batched tile-load maps), freed with it
 };
 
 }  // namespace
@@ -134,6 +135,7 @@ struct fv_ctx {
   unsigned long long *b_smax;      // [2][ngrids], then the FP32 lower bounds [2][ngrids]
   double *b_tacc;                  // [ngrids]
   unsigned *b_bar;                 // count, generation
+  unsigned *b_chunk_hi;            // per 32-cell chunk of each time-step item: its certified upper bound
   int b_total_tiles, b_total_chunks, b_blocks;
 };
 
@@ -196,10 +198,9 @@ void ntiles(const fv_grid &g, const int tile[3], int nt[3]) {
   for (int d = 0; d < 3; ++d) nt[d] = (d < g.dim) ? (g.n[d] + tile[d] - 1) / tile[d] : 1;
 }
 
-// TMA tensor map over a state array: dims (x, y[, z], var), box = tile + halo
-// (one z-plane for the z-marching kernel).
-bool make_tmap(const fv_ctx *c, const double *U, const int tile[3], int march, CUtensorMap *map) {
-  const fv_grid &g = c->grid;
+// TMA tensor map over the state array U (nv variables) of grid g: dims
+// (x, y[, z], var), box = tile + halo (one z-plane for the z-marching kernel).
+bool make_tmap_grid(const fv_grid &g, int nv, const double *U, const int tile[3], int march, CUtensorMap *map) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   if (g.n[0] % 2) return false;                          // row stride must be a multiple of 16 bytes
@@ -217,12 +218,16 @@ bool make_tmap(const fv_ctx *c, const double *U, const int tile[3], int march, C
     stride *= (cuuint64_t)g.n[d];
     strides[d] = stride;  // byte stride of dimension d+1
   }
-  dims[g.dim] = (cuuint64_t)c->nv;
-  boxd[g.dim] = (cuuint32_t)c->nv;
+  dims[g.dim] = (cuuint64_t)nv;
+  boxd[g.dim] = (cuuint32_t)nv;
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<double *>(U), dims, strides,
                    boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+bool make_tmap(const fv_ctx *c, const double *U, const int tile[3], int march, CUtensorMap *map) {
+  return make_tmap_grid(c->grid, c->nv, U, tile, march, map);
 }
 
 // Faces per axis of the split kernels: (n_d + 1) x the other extents.
@@ -435,8 +440,13 @@ int set_attributes(fv_ctx *c) {
   return FV_OK;
 }
 
+void destroy_graph(GraphEntry &g) {
+  cudaGraphExecDestroy(g.exec);
+  if (g.aux) cudaFree(g.aux);
+}
+
 void drop_graphs(fv_ctx *c) {
-  for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto &g : c->graphs) destroy_graph(g);
   c->graphs.clear();
 }
 
@@ -448,7 +458,7 @@ void remember_graph(fv_ctx *c, const GraphEntry &e) {
   // graph of e.U that it is about to launch)
   for (size_t i = 0; c->graphs.size() >= kMaxGraphs && i < c->graphs.size();) {
     if (c->graphs[i].U != e.U) {
-      cudaGraphExecDestroy(c->graphs[i].exec);
+      destroy_graph(c->graphs[i]);
       c->graphs.erase(c->graphs.begin() + i);
     } else {
       ++i;
@@ -529,6 +539,9 @@ int batch_init(fv_ctx *c, const fv_grid *grids, int ngrids) {
   FV_CK(cudaMalloc(&c->b_tacc, sizeof(double) * ngrids));
   FV_CK(cudaMalloc(&c->b_bar, sizeof(unsigned) * 2));
   FV_CK(cudaMemset(c->b_bar, 0, sizeof(unsigned) * 2));
+  long long chunks = 0;  // time-step items, as batch_setup counts them
+  for (int g = 0; g < ngrids; ++g) chunks += ((long long)grids[g].n[0] * grids[g].n[1] + kBatchChunk - 1) / kBatchChunk;
+  FV_CK(cudaMalloc(&c->b_chunk_hi, sizeof(unsigned) * (size_t)chunks * (kBatchChunk / 32)));
   return FV_OK;
 }
 
@@ -552,6 +565,7 @@ int batch_run(fv_ctx *c, double *Ud, int nsteps, double dt_fixed, bool want_t) {
     b.total_chunks = c->b_total_chunks;
     b.nsteps = nsteps;
     b.chunk_cells = kBatchChunk;
+    b.chunk_hi = c->b_chunk_hi;
     b.tile[0] = c->launch.stage[0].tile[0];
     b.tile[1] = c->launch.stage[0].tile[1];
     b.U = Ud;
@@ -572,6 +586,37 @@ int batch_run(fv_ctx *c, double *Ud, int nsteps, double dt_fixed, bool want_t) {
     b.inv2efix = c->scheme.efix > 0.0 ? 0.5 / c->scheme.efix : 0.0;
     b.cfl = c->scheme.cfl;
     b.dt_fixed = dt_fixed > 0.0 ? dt_fixed : 0.0;
+    // TMA tile loads: per stage source (Ud, U1, U2) and problem a tensor map
+    // over that problem's block, where its grid allows one (the conditions of
+    // single grids); the others load with plain loads.  The maps hold Ud's
+    // address, so they belong to this graph and are freed with it.
+    void *aux = nullptr;
+    if (c->launch.stage[0].loader == FV_LOADER_TMA) {
+      const int t3[3] = {b.tile[0], b.tile[1], 1};
+      std::vector<CUtensorMap> maps(3 * (size_t)n);
+      std::vector<int> ok(3 * (size_t)n, 0);
+      const double *src[3] = {Ud, c->U1, c->U2};
+      int any = 0;
+      for (int k = 0; k < 3; ++k)
+        for (int g = 0; g < n; ++g) {
+          memset(&maps[(size_t)k * n + g], 0, sizeof(CUtensorMap));
+          ok[(size_t)k * n + g] = make_tmap_grid(c->grids[g], 4, src[k] + c->offsets[g], t3, 0, &maps[(size_t)k * n + g]);
+          any |= ok[(size_t)k * n + g];
+        }
+      if (any) {
+        const size_t mb = sizeof(CUtensorMap) * maps.size();
+        FV_CK(cudaMalloc(&aux, mb + sizeof(int) * ok.size()));
+        cudaError_t em = cudaMemcpy(aux, maps.data(), mb, cudaMemcpyHostToDevice);
+        if (em == cudaSuccess)
+          em = cudaMemcpy(static_cast<char *>(aux) + mb, ok.data(), sizeof(int) * ok.size(), cudaMemcpyHostToDevice);
+        if (em != cudaSuccess) {
+          cudaFree(aux);
+          return cuda_fail(em);
+        }
+        b.tmaps = static_cast<const CUtensorMap *>(aux);
+        b.tma_ok = reinterpret_cast<const int *>(static_cast<char *>(aux) + mb);
+      }
+    }
     const int blocks = c->b_blocks < c->b_total_tiles ? c->b_blocks : c->b_total_tiles;
     cudaGraph_t graph;
     FV_CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -583,13 +628,22 @@ int batch_run(fv_ctx *c, double *Ud, int nsteps, double dt_fixed, bool want_t) {
     cudaError_t ec = cudaStreamEndCapture(c->cap, &graph);
     if (e != cudaSuccess) {
       if (ec == cudaSuccess) cudaGraphDestroy(graph);
+      if (aux) cudaFree(aux);
       return cuda_fail(e);
     }
-    FV_CK(ec);
+    if (ec != cudaSuccess) {
+      if (aux) cudaFree(aux);
+      return cuda_fail(ec);
+    }
     cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
-    FV_CK(ei);
-    remember_graph(c, GraphEntry{Ud, dbits, nsteps, exec});
+    if (ei != cudaSuccess) {
+      if (aux) cudaFree(aux);
+      return cuda_fail(ei);
+    }
+    GraphEntry ge{Ud, dbits, nsteps, exec};
+    ge.aux = aux;
+    remember_graph(c, ge);
   }
   FV_CK(cudaGraphLaunch(exec, c->stream));
   (void)want_t;
@@ -831,6 +885,7 @@ int fv_residual(fv_ctx *c, const double *U, double *R, double *rnorm2) {
   if (c->b_smax) cudaFree(c->b_smax);
   if (c->b_tacc) cudaFree(c->b_tacc);
   if (c->b_bar) cudaFree(c->b_bar);
+  if (c->b_chunk_hi) cudaFree(c->b_chunk_hi);
       c->norm_part = nullptr;
       c->norm_part_cap = 0;
       FV_CK(cudaMalloc(&c->norm_part, sizeof(double) * c->nv * nblk));
@@ -1044,7 +1099,9 @@ int adjoint(fv_ctx *c, const double *U, const double *lam, double *out, double w
   a.cA = cA;
   a.cB = cB;
   a.cC = cC;
-  const int tile2[3] = {16, 16, 1}, tile3[3] = {8, 4, 4};
+  // 2D: 16x20 tiles, 380 x-faces and 368 y-faces, each about two full
+  // rounds of the 192 threads (16x16 left 304 faces per axis, 1.6 rounds)
+  const int tile2[3] = {16, 20, 1}, tile3[3] = {8, 4, 4};
   const int *tile = g.dim == 2 ? tile2 : tile3;
   for (int d = 0; d < 3; ++d) {
     a.n[d] = g.n[d];
@@ -1125,6 +1182,7 @@ void fv_destroy(fv_ctx *c) {
   if (c->b_smax) cudaFree(c->b_smax);
   if (c->b_tacc) cudaFree(c->b_tacc);
   if (c->b_bar) cudaFree(c->b_bar);
+  if (c->b_chunk_hi) cudaFree(c->b_chunk_hi);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }

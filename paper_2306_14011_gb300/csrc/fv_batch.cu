@@ -7,8 +7,9 @@
 // (problem, cell chunk) or (problem, tile) -- are spread round-robin over all
 // co-resident CTAs; a grid-wide barrier separates the phases.  Each problem
 // keeps its own time step.  Tiles are processed by the same tile_work routine
-// as the single-grid stage kernels (plain loads), so every problem's results
-// are bitwise those of a single-grid run.
+// as the single-grid stage kernels -- TMA tile loads where the problem's grid
+// allows them, plain loads elsewhere -- so every problem's results are
+// bitwise those of a single-grid run.
 #include "fv_stage.cuh"
 
 namespace fvk {
@@ -56,11 +57,14 @@ __device__ __forceinline__ int find_problem(const int *begin, int nprob, int ite
   return lo;
 }
 
+// The CTA's mbarrier for TMA tile loads completes one phase per load;
+// `phase` is the parity of the next one.
 template <int MODE>
-__device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double *tile, double *s_coef,
-                                            double (*red)[32]) {
+__device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double *tile, uint64_t *mbar,
+                                            uint32_t &phase, double *s_coef, double (*red)[32]) {
   const double *Us = MODE == MODE_STAGE1 ? b.U : (MODE == MODE_STAGE2 ? b.U1 : b.U2);
   double *out = MODE == MODE_STAGE1 ? b.U1 : (MODE == MODE_STAGE2 ? b.U2 : b.U);
+  const int src = MODE == MODE_STAGE1 ? 0 : (MODE == MODE_STAGE2 ? 1 : 2);
   for (int item = blockIdx.x; item < b.total_tiles; item += gridDim.x) {
     const int p = find_problem(b.tile_begin, b.nprob, item);
     const BatchProblem &P = b.prob[p];
@@ -85,7 +89,8 @@ __device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double
       a.ds[d] = 0.0;
       a.inv_h[d] = d < 2 ? P.inv_h[d] : 0.0;
     }
-    a.use_tma = 0;
+    const CUtensorMap *map = b.tmaps ? b.tmaps + (size_t)src * b.nprob + p : nullptr;
+    a.use_tma = (map && b.tma_ok[(size_t)src * b.nprob + p]) ? 1 : 0;
     a.limiter = FV_LIM_MINMOD;
     a.recon = FV_RECON_CONSERVED;
     a.cL = a.cR = 0.0;
@@ -101,16 +106,25 @@ __device__ __forceinline__ bool stage_phase(const BatchArgs &b, int slot, double
     a.S = nullptr;
     a.vol = 0.0;
     const int local = item - b.tile_begin[p];
-    tile_work<2, MODE>(nullptr, a, local % P.ntile[0], local / P.ntile[0], 0, tile, nullptr, 0u, s_coef, red);
-    __syncthreads();  // the next item reuses the shared buffers
+    if (!tile_work<2, MODE>(map, a, local % P.ntile[0], local / P.ntile[0], 0, tile, mbar, phase, s_coef, red))
+      return false;  // a tile load timed out (flagged); the other CTAs' barrier waits run out
+    if (a.use_tma) phase ^= 1u;
+    // the next item reuses the shared buffers: this item's generic-proxy
+    // accesses of the tile box are ordered before the next TMA write to it
+    fence_proxy_async_smem();
+    __syncthreads();
   }
   return grid_barrier(b.bar_count, b.bar_gen, b.flags);
 }
 
 // Per problem, the largest certified FP32 lower bound of the wave-speed sum
-// (as in dt_bound_kernel), for problems where the pre-selection applies.
+// (as in dt_bound_kernel), for problems where the pre-selection applies, and
+// per 32-cell chunk (one warp) of each item the largest certified upper
+// bound (+inf when a cell of the chunk is not certified).
 __device__ __forceinline__ void dt_bound_phase(const BatchArgs &b, int slot) {
   __shared__ unsigned wmax[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per_item = (int)(b.chunk_cells / 32);
   for (int item = blockIdx.x; item < b.total_chunks; item += gridDim.x) {
     const int p = find_problem(b.chunk_begin, b.nprob, item);
     const BatchProblem &P = b.prob[p];
@@ -118,21 +132,29 @@ __device__ __forceinline__ void dt_bound_phase(const BatchArgs &b, int slot) {
     const long long N = (long long)P.n[0] * P.n[1];
     const long long c0 = (long long)(item - b.chunk_begin[p]) * b.chunk_cells;
     const long long c1 = c0 + b.chunk_cells < N ? c0 + b.chunk_cells : N;
+    const int nsub = (int)((c1 - c0 + 31) / 32);
     const double *U = b.U + P.off;
     unsigned best = 0u;
-    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-      float s32, rel;
-      if (wave_sum32<2>(U, N, c, b.g1f, b.gammaf, P.inv_hf, s32, rel)) {
-        const unsigned lo = __float_as_uint(__fmul_rd(s32, __fsub_rd(1.0f, rel)));
-        best = lo > best ? lo : best;
+    for (int q = warp; q < nsub; q += nw) {
+      const long long c = c0 + (long long)q * 32 + lane;
+      unsigned hi = 0u;
+      if (c < c1) {
+        float s32, rel;
+        if (wave_sum32<2>(U, N, c, b.g1f, b.gammaf, P.inv_hf, s32, rel)) {
+          const unsigned lo = __float_as_uint(__fmul_rd(s32, __fsub_rd(1.0f, rel)));
+          best = lo > best ? lo : best;
+          hi = __float_as_uint(__fmul_ru(s32, __fadd_ru(1.0f, rel)));
+        } else {
+          hi = 0x7f800000u;  // +inf: the chunk must be evaluated
+        }
       }
+      hi = __reduce_max_sync(0xffffffffu, hi);
+      if (lane == 0) b.chunk_hi[(long long)item * per_item + q] = hi;
     }
     best = __reduce_max_sync(0xffffffffu, best);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) wmax[warp] = best;
     __syncthreads();
     if (warp == 0) {
-      const int nw = (blockDim.x + 31) >> 5;
       const unsigned m = __reduce_max_sync(0xffffffffu, lane < nw ? wmax[lane] : 0u);
       if (lane == 0) atomicMax(b.lbound + (long long)slot * b.nprob + p, m);
     }
@@ -141,27 +163,29 @@ __device__ __forceinline__ void dt_bound_phase(const BatchArgs &b, int slot) {
 }
 
 // Per problem max over its cells of sum_d (|u_d| + c) / dx_d (as in dt_kernel:
-// cells whose certified FP32 upper bound is below the problem's lower bound
-// are skipped, every other cell is evaluated in FP64).
+// a 32-cell chunk whose certified FP32 upper bound is below the problem's
+// certified lower bound cannot hold the maximum and is skipped without
+// reading it; every other cell is evaluated in FP64).
 __device__ __forceinline__ void dt_phase(const BatchArgs &b, int slot) {
   __shared__ unsigned long long wmax[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per_item = (int)(b.chunk_cells / 32);
   for (int item = blockIdx.x; item < b.total_chunks; item += gridDim.x) {
     const int p = find_problem(b.chunk_begin, b.nprob, item);
     const BatchProblem &P = b.prob[p];
     const long long N = (long long)P.n[0] * P.n[1];
     const long long c0 = (long long)(item - b.chunk_begin[p]) * b.chunk_cells;
     const long long c1 = c0 + b.chunk_cells < N ? c0 + b.chunk_cells : N;
+    const int nsub = (int)((c1 - c0 + 31) / 32);
     const double *U = b.U + P.off;
-    const float L = P.bounded ? __uint_as_float(b.lbound[(long long)slot * b.nprob + p]) : 0.0f;
+    const unsigned L = P.bounded ? b.lbound[(long long)slot * b.nprob + p] : 0u;
     unsigned long long best = 0ull;
     bool bad = false;
-    for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-      if (P.bounded) {
-        float s32, rel;
-        if (wave_sum32<2>(U, N, c, b.g1f, b.gammaf, P.inv_hf, s32, rel) &&
-            __fmul_ru(s32, __fadd_ru(1.0f, rel)) < L)
-          continue;
-      }
+    for (int q = warp; q < nsub; q += nw) {
+      // non-negative float bits order like the values
+      if (P.bounded && b.chunk_hi[(long long)item * per_item + q] < L) continue;
+      const long long c = c0 + (long long)q * 32 + lane;
+      if (c >= c1) continue;
       const double rho = U[c];
       if (not_positive_finite(rho)) {
         bad = true;
@@ -188,11 +212,9 @@ __device__ __forceinline__ void dt_phase(const BatchArgs &b, int slot) {
       const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
       best = o > best ? o : best;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) wmax[warp] = best;
     const int anybad = __syncthreads_or(bad);
     if (warp == 0) {
-      const int nw = (blockDim.x + 31) >> 5;
       unsigned long long m = lane < nw ? wmax[lane] : 0ull;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) {
@@ -213,6 +235,19 @@ __global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) batch_run_kernel(con
   __shared__ double s_coef[5];
   __shared__ double red[4][32];
   double *tile = aligned_smem(smem_raw);
+  StageArgs ga;  // only the tile shape, for the mbarrier's place after the stage buffers
+  ga.tile[0] = b.tile[0];
+  ga.tile[1] = b.tile[1];
+  ga.tile[2] = 1;
+  uint64_t *mbar = stage_mbar<2>(tile, ga);
+  uint32_t phase = 0u;
+  if (b.tmaps) {
+    if (threadIdx.x == 0) {
+      mbar_init(smem_u32(mbar), 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
   for (int step = 0; step < b.nsteps; ++step) {
     const int slot = step & 1;
     if (b.dt_fixed <= 0.0) {
@@ -231,9 +266,9 @@ __global__ void __launch_bounds__(256, FV_STAGE_MIN_BLOCKS) batch_run_kernel(con
       for (int p = threadIdx.x; p < b.nprob; p += blockDim.x)
         b.t_acc[p] += b.dt_fixed > 0.0 ? b.dt_fixed
                                        : b.cfl / __longlong_as_double((long long)b.smax[(long long)slot * b.nprob + p]);
-    if (!stage_phase<MODE_STAGE1>(b, slot, tile, s_coef, red)) return;
-    if (!stage_phase<MODE_STAGE2>(b, slot, tile, s_coef, red)) return;
-    if (!stage_phase<MODE_STAGE3>(b, slot, tile, s_coef, red)) return;
+    if (!stage_phase<MODE_STAGE1>(b, slot, tile, mbar, phase, s_coef, red)) return;
+    if (!stage_phase<MODE_STAGE2>(b, slot, tile, mbar, phase, s_coef, red)) return;
+    if (!stage_phase<MODE_STAGE3>(b, slot, tile, mbar, phase, s_coef, red)) return;
   }
 }
 

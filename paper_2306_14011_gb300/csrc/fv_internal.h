@@ -91,7 +91,8 @@ struct BatchArgs {
   const int *tile_begin;   // [nprob + 1] first tile item of each problem
   const int *chunk_begin;  // [nprob + 1] first time-step chunk of each problem
   int nprob, total_tiles, total_chunks, nsteps;
-  long long chunk_cells;
+  long long chunk_cells;    // cells per time-step item (a multiple of 32)
+  unsigned *chunk_hi;       // [total_chunks][chunk_cells / 32] certified upper bound per 32-cell chunk
   int tile[2];
   double *U, *U1, *U2;           // packed states
   unsigned long long *smax;      // [2][nprob] bits of each problem's max wave-speed sum
@@ -99,6 +100,8 @@ struct BatchArgs {
   double *t_acc;                 // [nprob] simulated time, or null
   unsigned *flags;
   unsigned *bar_count, *bar_gen; // grid barrier words
+  const CUtensorMap *tmaps;      // [3][nprob] tile-load maps over U, U1, U2 per problem, or null
+  const int *tma_ok;             // [3][nprob] 1 where that map exists (else plain loads)
   double g1, gamma, half_eps, efix, inv2efix, cfl, dt_fixed;
   float g1f, gammaf;
 };

@@ -53,10 +53,6 @@ __host__ __device__ inline MarchGeom march_geom(const int tile[3]) {
   return g;
 }
 
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // Plain loads of a whole plane box (interior and x-y halo) of plane zsrc.
 __device__ __forceinline__ void load_plane_plain(double *slot, const StageArgs &a, const int o[2], int ext0,
                                                  int ext1, int zsrc, const MarchGeom &G) {

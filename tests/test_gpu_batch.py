@@ -29,13 +29,21 @@ def _single(g, U, nsteps, dt_fixed=0.0):
         return Ud.cpu().numpy(), t
 
 
+@pytest.mark.parametrize("loader", [fv.FV_LOADER_TMA, fv.FV_LOADER_PLAIN])
 @pytest.mark.parametrize("dt_fixed", [0.0, 2e-4])
-def test_small_batch_matches_single_grid_runs_and_oracle(dt_fixed):
+def test_small_batch_matches_single_grid_runs_and_oracle(dt_fixed, loader):
+    """Sizes below and above the tile + halo box, odd and even widths: with
+    the TMA loader the even ones of at least 36 cells load by TMA, the others
+    by plain loads; with the plain loader all of them."""
     rng = np.random.default_rng(11)
     specs = [(int(n), float(th)) for n, th in zip([8, 13, 16, 31, 40, 47, 64, 70, 5], rng.uniform(0, 2 * np.pi, 9))]
     probs = _problems(specs)
     grids = [g for g, _ in probs]
     with fv.Solver(grids) as s:
+        d = s.launch
+        for st in d["stage"]:
+            st["loader"] = loader
+        s.launch = d
         assert s.offsets[0] == 0 and all(o % 32 == 0 for o in s.offsets)
         U = s.pack([torch.from_numpy(u).cuda() for _, u in probs])
         t = s.run(U, 10, dt_fixed, return_time=True)
@@ -51,7 +59,8 @@ def test_small_batch_matches_single_grid_runs_and_oracle(dt_fixed):
 
 def test_batched_sod_config_96_problems_50_steps():
     """96 rotated Sod problems, sizes log-uniform in [64, 2048] (seed 3),
-    transmissive boundaries, 50 CFL steps in one persistent launch."""
+    transmissive boundaries, 50 CFL steps in one persistent launch (the
+    default launch: TMA tile loads for the even widths)."""
     specs = I.batched_sod(96, seed=3)
     probs = _problems(specs)
     grids = [g for g, _ in probs]
