@@ -66,14 +66,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # dram__bytes_write.sum, full 4096^2 launches, mean of the three stages of one
 # step), valid for the kernel sources whose hash and the launch shape recorded
 # with it; null otherwise.
-STAGE_TRAFFIC = {"bytes": 1.3893e9, "source_hash": "6bc4056cc9b5ba98", "tile": [64, 16, 1], "threads": 192}
+STAGE_TRAFFIC = {"bytes": 1.3892e9, "source_hash": "68847fbb2e4d39b5", "tile": [64, 16, 1], "threads": 192}
 # FP64 instructions the fused stage kernels execute per cell and stage (ncu
 # sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on, mean of the three
 # stages at 2048^2 / 192^3), for the kernel sources with this hash; and the
 # FP64 products evaluated on the integer pipe instead: 29 per face in 2D and 32
 # in 3D (the Roe flux's products), times the faces per cell of the default
 # tiles (2.078 for 64x16, 3.375 for 8x8x8).
-STAGE_FP64_INST = {"2d": 114.3, "3d": 231.2, "source_hash": "6bc4056cc9b5ba98"}
+STAGE_FP64_INST = {"2d": 114.3, "3d": 231.2, "source_hash": "68847fbb2e4d39b5"}
 INT_PIPE_PRODUCTS = {"2d": 60.3, "3d": 108.0}
 
 
@@ -320,7 +320,7 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded Kelvin-Helmholtz initial condition)",
+        "data": W["data"],
         "config": {"workload": W["desc"], "cells": cells, "launch": args.launch or "default",
                    "launch_params": solver.launch,
                    "kernel_structure": ("split: per stage %d kernels (limiter and flux per axis, source, RHS, "
@@ -483,6 +483,7 @@ def make_workload(args, I):
         n = args.n
         g, U0 = I.kelvin_helmholtz(n, seed=1)
         return dict(name="kh4096", grid=g, U0=U0, cells=g.ncells, batched=False, flop=FLOP_PER_CELL_STAGE_2D,
+                    data="synthetic (seeded Kelvin-Helmholtz initial condition)",
                     bytes=BYTES_PER_CELL_STAGE_2D, kernel="fvk::stage_kernel<2, stage>", launches_per_step=5,
                     metric=METRIC,
                     desc=f"2D Euler Kelvin-Helmholtz {n}x{n} periodic, FP64, MUSCL-minmod + Roe + SSP-RK3, CFL 0.5; "
@@ -493,6 +494,7 @@ def make_workload(args, I):
         n = 384 if args.n == N_CELLS_SIDE else args.n
         g, U0 = I.taylor_green(n, seed=2)
         return dict(name="tgv384", grid=g, U0=U0, cells=g.ncells, batched=False, flop=FLOP_PER_CELL_STAGE_3D,
+                    data="synthetic (Taylor-Green vortex initial condition, seeded pressure noise)",
                     bytes=BYTES_PER_CELL_STAGE_3D, kernel="fvk::stage_kernel<3, stage>", launches_per_step=5,
                     metric=f"FP64 cell-updates/s per RK stage (3D Euler Taylor-Green {n}^3)",
                     desc=f"3D Euler Taylor-Green {n}^3 periodic, M=0.1, 1e-4 pressure noise, FP64, MUSCL-minmod + "
@@ -503,6 +505,7 @@ def make_workload(args, I):
     grids = [p[0] for p in probs]
     cells = sum(gg.ncells for gg in grids)
     return dict(name="sod96", grid=grids, U0=None, states=[p[1] for p in probs], cells=cells, batched=True,
+                data="synthetic (rotated Sod shock-tube initial conditions, seeded sizes and angles)",
                 flop=FLOP_PER_CELL_STAGE_2D, bytes=BYTES_PER_CELL_STAGE_2D,
                 kernel="fvk::batch_run_kernel (persistent, all steps)", launches_per_step=1,
                 metric="FP64 cell-updates/s per RK stage (96 batched 2D Sod grids, 64^2..2048^2)",

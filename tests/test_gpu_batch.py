@@ -32,11 +32,13 @@ def _single(g, U, nsteps, dt_fixed=0.0):
 @pytest.mark.parametrize("loader", [fv.FV_LOADER_TMA, fv.FV_LOADER_PLAIN])
 @pytest.mark.parametrize("dt_fixed", [0.0, 2e-4])
 def test_small_batch_matches_single_grid_runs_and_oracle(dt_fixed, loader):
-    """Sizes below and above the tile + halo box, odd and even widths: with
-    the TMA loader the even ones of at least 36 cells load by TMA, the others
-    by plain loads; with the plain loader all of them."""
+    """Sizes below, at and above the 36-cell tile + halo box of the 32x32
+    tiles, odd and even widths: with the TMA loader the even ones of at least
+    36 cells load by TMA (36: the box spans the whole grid), the others by
+    plain loads; with the plain loader all of them."""
     rng = np.random.default_rng(11)
-    specs = [(int(n), float(th)) for n, th in zip([8, 13, 16, 31, 40, 47, 64, 70, 5], rng.uniform(0, 2 * np.pi, 9))]
+    sizes = [8, 13, 16, 31, 40, 47, 64, 70, 5, 36, 35]
+    specs = [(int(n), float(th)) for n, th in zip(sizes, rng.uniform(0, 2 * np.pi, len(sizes)))]
     probs = _problems(specs)
     grids = [g for g, _ in probs]
     with fv.Solver(grids) as s:
