@@ -74,31 +74,39 @@ __device__ void load_box(double *dst, const double *src, const AdjArgs &a, const
   }
 }
 
+// pick3(d, x, y, z): x, y or z for d = 0, 1, 2 (register selects, so that an
+// axis chosen at run time needs no indexed local array).
+__device__ __forceinline__ int pick3(int d, int x, int y, int z) { return d == 0 ? x : (d == 1 ? y : z); }
+
 // Faces along axis D: per face the cotangents sent to its four stencil cells
 // (c0..c3 for cells f-2 .. f+1), stored as 4*NV doubles; then every tile cell
-// gathers and accumulates scale * (sum) into acc.
+// gathers and accumulates scale * (sum) into acc.  The axis is a run-time
+// argument: the kernel runs one copy of this (long) code for every axis, half
+// (2D) or a third (3D) of the instruction footprint of one copy per axis,
+// and the normal-first ordering of the flux's variables is formed with
+// selects.
 // HALF: the MUSCL factor eps/2 is 1/2 (eps = 1), so h * x is an exponent
 // decrement on the integer pipe (scale_pow2) instead of an FP64 product.
-template <int DIM, int D, bool HALF>
+template <int DIM, bool HALF>
 __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb, double *acc, const AdjArgs &a,
-                              const int o[3], const int ext[3], const AdjGeom &G, double scale) {
+                              const int o[3], const int ext[3], const AdjGeom &G, double scale, int D) {
   constexpr int NV = DIM + 2;
   constexpr int NT = DIM - 1;
   constexpr int E = NV - 1;
   const int fe0 = ext[0] + (D == 0 ? 3 : 0), fe1 = ext[1] + (D == 1 ? 3 : 0);
   const int fe2 = DIM == 3 ? ext[2] + (D == 2 ? 3 : 0) : 1;
   const int nf = fe0 * fe1 * fe2;
-  const int us = D == 0 ? 1 : (D == 1 ? G.UX : G.UX * G.UY);  // U stencil stride
-  const int ls = D == 0 ? 1 : (D == 1 ? G.LX : G.LX * G.LY);  // lam stride
+  const int us = pick3(D, 1, G.UX, G.UX * G.UY);  // U stencil stride
+  const int ls = pick3(D, 1, G.LX, G.LX * G.LY);  // lam stride
+  const int oD = pick3(D, o[0], o[1], o[2]), nD = pick3(D, a.n[0], a.n[1], a.n[2]);
   const double h = a.half_eps;
   const bool lo_trans = a.bc[D][0] == FV_BC_TRANSMISSIVE, hi_trans = a.bc[D][1] == FV_BC_TRANSMISSIVE;
   for (int f = threadIdx.x; f < nf; f += blockDim.x) {
     const int i = f % fe0, rr = f / fe0, j = rr % fe1, k = rr / fe1;
     // face index along D (global): between cells fg-1 and fg
-    const int loc[3] = {i, j, k};
-    const int fg = o[D] - 1 + loc[D];
+    const int fg = oD - 1 + pick3(D, i, j, k);
     double *out = Fb + f;  // 4*NV values at stride G.fmax
-    const bool real = !((lo_trans && fg < 0) || (hi_trans && fg > a.n[D]));
+    const bool real = !((lo_trans && fg < 0) || (hi_trans && fg > nD));
     if (!real) {
 #pragma unroll
       for (int q = 0; q < 4 * NV; ++q) out[q * G.fmax] = 0.0;
@@ -123,41 +131,57 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
       pR[v] = minmod_pick(d0, dp);
       gb[v] = pl[v * G.lplane] - pl[v * G.lplane + ls];
     }
+    // normal-first ordering (rho, m_D, tangential momenta in axis order, E)
     double qL[NT + 3], qR[NT + 3], Gb[NT + 3], bL[NT + 3], bR[NT + 3];
     qL[0] = QL[0];
     qR[0] = QR[0];
     Gb[0] = gb[0];
-    qL[1] = QL[1 + D];
-    qR[1] = QR[1 + D];
-    Gb[1] = gb[1 + D];
-    int t = 0;
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      if (ax == D) continue;
-      qL[2 + t] = QL[1 + ax];
-      qR[2 + t] = QR[1 + ax];
-      Gb[2 + t] = gb[1 + ax];
-      ++t;
-    }
     qL[E] = QL[E];
     qR[E] = QR[E];
     Gb[E] = gb[E];
+    if (DIM == 2) {
+      const bool x = D == 0;
+      qL[1] = isel(x, QL[1], QL[2]);
+      qL[2] = isel(x, QL[2], QL[1]);
+      qR[1] = isel(x, QR[1], QR[2]);
+      qR[2] = isel(x, QR[2], QR[1]);
+      Gb[1] = isel(x, gb[1], gb[2]);
+      Gb[2] = isel(x, gb[2], gb[1]);
+    } else {
+      // normal m_D; tangential (m_1, m_2), (m_0, m_2) or (m_0, m_1)
+      const bool d0 = D == 0, d2 = D == 2;
+      qL[1] = isel(d0, QL[1], isel(d2, QL[3], QL[2]));
+      qL[2] = isel(d0, QL[2], QL[1]);
+      qL[3] = isel(d2, QL[2], QL[3]);
+      qR[1] = isel(d0, QR[1], isel(d2, QR[3], QR[2]));
+      qR[2] = isel(d0, QR[2], QR[1]);
+      qR[3] = isel(d2, QR[2], QR[3]);
+      Gb[1] = isel(d0, gb[1], isel(d2, gb[3], gb[2]));
+      Gb[2] = isel(d0, gb[2], gb[1]);
+      Gb[3] = isel(d2, gb[2], gb[3]);
+    }
     roe_F_vjp<NT>(qL, qR, a.g1, a.efix, a.inv2efix, Gb, bL, bR);
+    // back to the natural variable order
     double QLb[NV], QRb[NV];
     QLb[0] = bL[0];
     QRb[0] = bR[0];
-    QLb[1 + D] = bL[1];
-    QRb[1 + D] = bR[1];
-    t = 0;
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      if (ax == D) continue;
-      QLb[1 + ax] = bL[2 + t];
-      QRb[1 + ax] = bR[2 + t];
-      ++t;
-    }
     QLb[E] = bL[E];
     QRb[E] = bR[E];
+    if (DIM == 2) {
+      const bool x = D == 0;
+      QLb[1] = isel(x, bL[1], bL[2]);
+      QLb[2] = isel(x, bL[2], bL[1]);
+      QRb[1] = isel(x, bR[1], bR[2]);
+      QRb[2] = isel(x, bR[2], bR[1]);
+    } else {
+      const bool d0 = D == 0, d1 = D == 1, d2 = D == 2;
+      QLb[1] = isel(d0, bL[1], bL[2]);
+      QLb[2] = isel(d1, bL[1], isel(d0, bL[2], bL[3]));
+      QLb[3] = isel(d2, bL[1], bL[3]);
+      QRb[1] = isel(d0, bR[1], bR[2]);
+      QRb[2] = isel(d1, bR[1], isel(d0, bR[2], bR[3]));
+      QRb[3] = isel(d2, bR[1], bR[3]);
+    }
     // through the reconstruction: QL = q1 + h mm(q1-q0, q2-q1), QR = q2 - h mm(q2-q1, q3-q2).
     // The picked slope's derivative is +-1 on its two cells; the selections and
     // sign flips run on the integer pipe (isel, mul_sign), only the sums in FP64.
@@ -185,16 +209,14 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
   // c2 of m, c3 of m-1 (local face index = global face - (o[D]-1)); boundary
   // cells of transmissive sides also collect what was sent to their ghosts.
   const int ncell = ext[0] * ext[1] * (DIM == 3 ? ext[2] : 1);
-  const int fstride = D == 0 ? 1 : (D == 1 ? fe0 : fe0 * fe1);
+  const int fstride = pick3(D, 1, fe0, fe0 * fe1);
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const int i = c % ext[0], rr = c / ext[0], j = rr % ext[1], k = rr / ext[1];
-    const int loc[3] = {i, j, k};
-    const int m = loc[D];
-    // face (m + 1) in local face coordinates sits at face index f0 below
-    int fi[3] = {i, j, k};
-    fi[D] = m + 1;  // local index of face between cells m-1 and m, i.e. global face o[D]+m
-    const int fc = (fi[2] * fe1 + fi[1]) * fe0 + fi[0];  // face "m" (global o[D]+m)
-    const int gcell = o[D] + m;
+    const int m = pick3(D, i, j, k);
+    // local index of the face between cells m-1 and m (global face o[D]+m) along D
+    const int fi = D == 0 ? m + 1 : i, fj = D == 1 ? m + 1 : j, fk = D == 2 ? m + 1 : k;
+    const int fc = (fk * fe1 + fj) * fe0 + fi;  // face "m" (global o[D]+m)
+    const int gcell = oD + m;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double *P = Fb + (4 * v) * G.fmax;
@@ -207,7 +229,7 @@ __device__ void adj_face_pass(const double *Ubox, const double *Lbox, double *Fb
         // (cell -1), face 1 sends c0 (cell -1)
         s += P[0 * G.fmax + fc] + P[1 * G.fmax + fc] + P[0 * G.fmax + fc + fstride];
       }
-      if (hi_trans && gcell == a.n[D] - 1) {
+      if (hi_trans && gcell == nD - 1) {
         // ghosts n, n+1 are copies of cell n-1: face n sends c2 (cell n) and c3
         // (cell n+1), face n-1 sends c3 (cell n)
         s += P[2 * G.fmax + fc + fstride] + P[3 * G.fmax + fc + fstride] + P[3 * G.fmax + fc];
@@ -247,9 +269,8 @@ __global__ void __launch_bounds__(DIM == 2 ? kAdjThreads2d : 256, DIM == 2 ? 2 :
   load_box<DIM>(Ubox, a.U, a, o, ext, 3, G.UX, G.UY, G.uplane, false);
   load_box<DIM>(Lbox, a.lam, a, o, ext, 2, G.LX, G.LY, G.lplane, true);
   __syncthreads();
-  adj_face_pass<DIM, 0, HALF>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[0]);
-  adj_face_pass<DIM, 1, HALF>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[1]);
-  if constexpr (DIM == 3) adj_face_pass<DIM, 2, HALF>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[2]);
+#pragma unroll 1
+  for (int D = 0; D < DIM; ++D) adj_face_pass<DIM, HALF>(Ubox, Lbox, Fb, acc, a, o, ext, G, a.scale[D], D);
   const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
   const int ncell = ext[0] * ext[1] * ext[2];
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
