@@ -49,6 +49,43 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
+typedef CUresult (*PointerAttributeFn)(void *, CUpointer_attribute, CUdeviceptr);
+
+PointerAttributeFn pointer_attribute_fn() {
+  static PointerAttributeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PointerAttributeFn>(p);
+  });
+  return fn;
+}
+
+// The device address of host memory [p, p + bytes) when the whole range lies
+// in one page-locked allocation mapped into the current device's address
+// space, so that kernels may store to it directly; nullptr otherwise
+// (pageable memory, or a range the driver cannot vouch for).
+double *mapped_host_range(double *p, size_t bytes) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  PointerAttributeFn get = pointer_attribute_fn();
+  if (!get) return nullptr;
+  CUdeviceptr start = 0;
+  size_t size = 0;
+  const CUdeviceptr d = reinterpret_cast<CUdeviceptr>(at.devicePointer);
+  if (get(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, d) != CUDA_SUCCESS ||
+      get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, d) != CUDA_SUCCESS)
+    return nullptr;
+  if (d < start || bytes > size || d - start > size - bytes) return nullptr;
+  return static_cast<double *>(at.devicePointer);
+}
 
 }  // namespace
 
@@ -955,10 +992,13 @@ int fv_rk_step(fv_ctx *c, double *U, double dt, double *dt_used) {
 }
 
 // The last SSP-RK3 step of a run on a host state: the dt reduction and
-// stages 1-2 as usual, then stage 3 in bands of whole tile rows (2D) or tile
-// planes (3D), each band's cells copied back to the host on a second stream
-// while the next band computes, so most of the device-to-host copy overlaps
-// the last kernel.
+// stages 1-2 as usual, then stage 3.  On page-locked host memory mapped into
+// the device's address space, stage 3 stores the new state straight to the
+// host over the host link (its ~120 GB/s of stores stay below the link's
+// rate, so the copy back costs no time of its own).  Otherwise stage 3 runs in
+// bands of whole tile rows (2D) or tile planes (3D), each band's cells copied
+// back to the host on a second stream while the next band computes, so most
+// of the device-to-host copy overlaps the last kernel.
 int last_step_to_host(fv_ctx *c, double *Ud, double *Uh, double dt_fixed, bool cfl) {
   const fv_grid &g = c->grid;
   const fv_kernel_cfg &k3 = c->launch.stage[2];
@@ -982,6 +1022,8 @@ int last_step_to_host(fv_ctx *c, double *Ud, double *Uh, double dt_fixed, bool c
   }
   if ((r = stage(c, MODE_STAGE1, 0, Ud, Ud, c->U1, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
   if ((r = stage(c, MODE_STAGE2, 1, c->U1, Ud, c->U2, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
+  if (double *Uh_dev = mapped_host_range(Uh, c->state_bytes))
+    return stage(c, MODE_STAGE3, 2, c->U2, Ud, Uh_dev, sm, dt_fixed, nullptr, c->t_acc, c->stream);
   const long long cells_per_unit = (long long)g.n[0] * (slow == 2 ? g.n[1] : 1);  // cells per grid row / plane
   const long long N = c->ncells;
   for (int b = 0; b < nb; ++b) {
