@@ -158,10 +158,13 @@ struct fv_ctx {
   long long norm_part_cap;
   double *X1, *X2;            // adjoint work states (lazy)
   double *split_buf;          // FV_SPLIT face states, fluxes and residual (lazy)
+  double *fd;                 // host-state runs: per-axis flux differences of the first stage (lazy)
+  std::vector<cudaEvent_t> h2d_events;  // host-state runs: per-band copy-in events (lazy)
   std::vector<GraphEntry> graphs;
   const double *source;        // caller's cell-averaged source of Eq. (5), or null
   // host-pointer runs: copy-back stream and per-band events (lazy)
   cudaStream_t copy_stream;
+  cudaStream_t aux_stream;  // host-state runs: second stream of the first stage's bands (lazy)
   std::vector<cudaEvent_t> band_events;
   // batched contexts (ngrids > 1)
   int ngrids;
@@ -403,6 +406,7 @@ int stage(fv_ctx *c, int mode, int sidx, const double *Us, const double *Un, dou
   a.dt_fixed = dt_fixed;
   a.t_acc = t_acc;
   a.flags = c->flags;
+  a.fd = c->fd;
   CUtensorMap map;
   memset(&map, 0, sizeof(map));
   a.march = k.march;
@@ -991,58 +995,165 @@ int fv_rk_step(fv_ctx *c, double *U, double dt, double *dt_used) {
   return FV_OK;
 }
 
-// The last SSP-RK3 step of a run on a host state: the dt reduction and
-// stages 1-2 as usual, then stage 3.  On page-locked host memory mapped into
-// the device's address space, stage 3 stores the new state straight to the
-// host over the host link (its ~120 GB/s of stores stay below the link's
-// rate, so the copy back costs no time of its own).  Otherwise stage 3 runs in
-// bands of whole tile rows (2D) or tile planes (3D), each band's cells copied
-// back to the host on a second stream while the next band computes, so most
-// of the device-to-host copy overlaps the last kernel.
-int last_step_to_host(fv_ctx *c, double *Ud, double *Uh, double dt_fixed, bool cfl) {
+// Host-state runs are split into bands of whole tile rows (2D) or tile
+// planes (3D) of stage launch sidx: band b holds tile rows [r0, r1) and the
+// grid rows [u0, u1) along the banded axis.
+struct Bands {
+  int slow;                 // banded axis: y in 2D, z in 3D
+  long long per_row;        // tiles per tile row / plane
+  int rows, nb;             // tile rows, bands
+  long long cells_per_unit; // cells per grid row / plane
+  int r0(int b) const { return (int)((long long)rows * b / nb); }
+};
+
+Bands make_bands(const fv_ctx *c, int sidx, int max_bands) {
   const fv_grid &g = c->grid;
-  const fv_kernel_cfg &k3 = c->launch.stage[2];
   int nt[3];
-  ntiles(g, k3.tile, nt);
-  const int slow = g.dim - 1;                     // banded axis: y in 2D, z in 3D
-  const long long per_row = (long long)nt[0] * (slow == 2 ? nt[1] : 1);  // tiles per tile row / plane
-  const int rows = nt[slow];
-  const int nb = rows < 8 ? rows : 8;
-  if (!c->copy_stream) FV_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-  while ((int)c->band_events.size() < nb + 1) {
+  ntiles(g, c->launch.stage[sidx].tile, nt);
+  Bands B;
+  B.slow = g.dim - 1;
+  B.per_row = (long long)nt[0] * (B.slow == 2 ? nt[1] : 1);
+  B.rows = nt[B.slow];
+  B.nb = B.rows < max_bands ? B.rows : max_bands;
+  B.cells_per_unit = (long long)g.n[0] * (B.slow == 2 ? g.n[1] : 1);
+  return B;
+}
+
+int ensure_events(std::vector<cudaEvent_t> &ev, int n) {
+  while ((int)ev.size() < n) {
     cudaEvent_t e;
     FV_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    c->band_events.push_back(e);
+    ev.push_back(e);
   }
+  return FV_OK;
+}
+
+// Whether the first stage of a host-state run may overlap the copy in: fused
+// box-tile stage 1 (the flux-difference mode has no z-marching variant) on a
+// grid whose tile rows (planes) are at least two cells high, so that a band's
+// 2-cell halo lies in its neighbours.
+bool overlap_first_stage(const fv_ctx *c) {
+  const fv_kernel_cfg &k1 = c->launch.stage[0];
+  return c->launch.mode == FV_FUSED && k1.march == 0 && k1.tile[c->grid.dim - 1] >= 2;
+}
+
+// Stage 1 of the first step of a run on a host state, overlapped with the
+// state's copy to the device: the copy runs band by band (whole tile rows in
+// 2D, tile planes in 3D) on the copy stream; as soon as a band and its
+// neighbours have arrived, the flux-difference kernel computes that band's
+// per-axis flux differences; the CFL reduction runs on the copy stream once
+// the last band is in; then an elementwise kernel forms U1 = U + dt L(U) from
+// the differences with the fused stage-1 kernel's operations in its order
+// (the same bits).
+int first_stage_from_host(fv_ctx *c, const double *Uh, double *Ud, double dt_fixed, bool cfl) {
+  const fv_grid &g = c->grid;
+  const Bands B = make_bands(c, 0, 1);  // geometry only: the bands are set here
+  const fv_kernel_cfg &k1 = c->launch.stage[0];
+  const long long N = c->ncells;
+  // bands of 1, 1, 1, 2, 4, 8 and then 16 tile rows: the first flux
+  // differences start once 3 tile rows are in, and the copy (about twice as
+  // fast as the flux kernel) stays ahead of the bands after them
+  std::vector<int> rb{0};
+  const int ramp[6] = {1, 1, 1, 2, 4, 8};
+  for (int q = 0; rb.back() < B.rows; ++q) rb.push_back(std::min(B.rows, rb.back() + (q < 6 ? ramp[q] : 16)));
+  const int nb = (int)rb.size() - 1;
+  if (!c->fd) FV_CK(cudaMalloc(&c->fd, sizeof(double) * (size_t)g.dim * c->state_bytes / sizeof(double)));
+  if (!c->copy_stream) FV_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  if (!c->aux_stream) FV_CK(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
   int r;
-  const unsigned long long *sm = nullptr;
-  if (cfl) {
-    if ((r = dt_launch(c, Ud, c->stream))) return r;
-    sm = c->smax;
+  if ((r = ensure_events(c->h2d_events, nb + 3))) return r;
+  // the copy in and the second band stream start after the compute stream's
+  // earlier work (which may still read Ud)
+  FV_CK(cudaEventRecord(c->h2d_events[nb + 1], c->stream));
+  FV_CK(cudaStreamWaitEvent(c->copy_stream, c->h2d_events[nb + 1], 0));
+  FV_CK(cudaStreamWaitEvent(c->aux_stream, c->h2d_events[nb + 1], 0));
+  for (int b = 0; b < nb; ++b) {
+    const long long u0 = (long long)rb[b] * k1.tile[B.slow];
+    const long long u1 = std::min<long long>((long long)rb[b + 1] * k1.tile[B.slow], g.n[B.slow]);
+    for (int v = 0; v < c->nv; ++v) {
+      const long long off = v * N + u0 * B.cells_per_unit;
+      FV_CK(cudaMemcpyAsync(Ud + off, Uh + off, sizeof(double) * (u1 - u0) * B.cells_per_unit,
+                            cudaMemcpyHostToDevice, c->copy_stream));
+    }
+    FV_CK(cudaEventRecord(c->h2d_events[b], c->copy_stream));
   }
-  if ((r = stage(c, MODE_STAGE1, 0, Ud, Ud, c->U1, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
-  if ((r = stage(c, MODE_STAGE2, 1, c->U1, Ud, c->U2, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
+  if (cfl && (r = dt_launch(c, Ud, c->copy_stream))) return r;
+  FV_CK(cudaEventRecord(c->h2d_events[nb], c->copy_stream));
+  // band b reads the rows of bands b-1..b+1 (the 2-cell halo; across a
+  // periodic boundary band 0 reads the last band and the last band band 0):
+  // bands 1..nb-2 start once band b+1 is in (the copies complete in order),
+  // the last band and band 0 once everything is.  Consecutive bands go to
+  // two streams, so that a band's last partial wave of CTAs overlaps the
+  // next band.
+  int nlaunch = 0;
+  auto band = [&](int b) {
+    cudaStream_t st = (nlaunch++ & 1) ? c->aux_stream : c->stream;
+    const int wait = (b == 0 || b + 1 >= nb) ? nb - 1 : b + 1;
+    const cudaError_t e = cudaStreamWaitEvent(st, c->h2d_events[wait], 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return stage(c, MODE_FLUXDIFF, 0, Ud, Ud, nullptr, nullptr, 0.0, nullptr, nullptr, st,
+                 (long long)rb[b] * B.per_row, (long long)(rb[b + 1] - rb[b]) * B.per_row);
+  };
+  for (int b = 1; b + 1 < nb; ++b)
+    if ((r = band(b))) return r;
+  if (nb > 1 && (r = band(nb - 1))) return r;
+  if ((r = band(0))) return r;
+  // U1 = U + dt L(U), after every band and the CFL reduction
+  FV_CK(cudaEventRecord(c->h2d_events[nb + 2], c->aux_stream));
+  FV_CK(cudaStreamWaitEvent(c->stream, c->h2d_events[nb + 2], 0));
+  FV_CK(cudaStreamWaitEvent(c->stream, c->h2d_events[nb], 0));
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  a.Us = Ud;
+  a.out = c->U1;
+  a.fd = c->fd;
+  a.S = c->source;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = g.n[d];
+    a.inv_h[d] = (d < g.dim) ? g.n[d] / g.len[d] : 1.0;  // as stage() forms it
+  }
+  a.smax = cfl ? c->smax : nullptr;
+  a.cfl = c->scheme.cfl;
+  a.dt_fixed = dt_fixed;
+  FV_CK(launch_stage1_from_fd(g.dim, a, c->stream));
+  return FV_OK;
+}
+
+// Stage 3 of the last SSP-RK3 step of a run on a host state.  On page-locked
+// host memory mapped into the device's address space, stage 3 stores the new
+// state straight to the host over the host link (its ~120 GB/s of stores stay
+// below the link's rate, so the copy back costs no time of its own).
+// Otherwise stage 3 runs in bands of whole tile rows (2D) or tile planes (3D),
+// each band's cells copied back to the host on a second stream while the
+// next band computes, so most of the device-to-host copy overlaps the last
+// kernel.
+int last_stage_to_host(fv_ctx *c, double *Ud, double *Uh, const unsigned long long *sm, double dt_fixed) {
+  const fv_grid &g = c->grid;
   if (double *Uh_dev = mapped_host_range(Uh, c->state_bytes))
     return stage(c, MODE_STAGE3, 2, c->U2, Ud, Uh_dev, sm, dt_fixed, nullptr, c->t_acc, c->stream);
-  const long long cells_per_unit = (long long)g.n[0] * (slow == 2 ? g.n[1] : 1);  // cells per grid row / plane
+  const Bands B = make_bands(c, 2, 8);
+  const fv_kernel_cfg &k3 = c->launch.stage[2];
+  if (!c->copy_stream) FV_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  int r;
+  if ((r = ensure_events(c->band_events, B.nb + 1))) return r;
   const long long N = c->ncells;
-  for (int b = 0; b < nb; ++b) {
-    const int r0 = (int)((long long)rows * b / nb), r1 = (int)((long long)rows * (b + 1) / nb);
-    if ((r = stage(c, MODE_STAGE3, 2, c->U2, Ud, Ud, sm, dt_fixed, nullptr, c->t_acc, c->stream, r0 * per_row,
-                   (long long)(r1 - r0) * per_row)))
+  for (int b = 0; b < B.nb; ++b) {
+    const int r0 = B.r0(b), r1 = B.r0(b + 1);
+    if ((r = stage(c, MODE_STAGE3, 2, c->U2, Ud, Ud, sm, dt_fixed, nullptr, c->t_acc, c->stream, r0 * B.per_row,
+                   (long long)(r1 - r0) * B.per_row)))
       return r;
     FV_CK(cudaEventRecord(c->band_events[b], c->stream));
     FV_CK(cudaStreamWaitEvent(c->copy_stream, c->band_events[b], 0));
-    const long long u0 = (long long)r0 * k3.tile[slow];
-    const long long u1 = std::min<long long>((long long)r1 * k3.tile[slow], g.n[slow]);
+    const long long u0 = (long long)r0 * k3.tile[B.slow];
+    const long long u1 = std::min<long long>((long long)r1 * k3.tile[B.slow], g.n[B.slow]);
     for (int v = 0; v < c->nv; ++v) {
-      const long long off = v * N + u0 * cells_per_unit;
-      FV_CK(cudaMemcpyAsync(Uh + off, Ud + off, sizeof(double) * (u1 - u0) * cells_per_unit, cudaMemcpyDeviceToHost,
-                            c->copy_stream));
+      const long long off = v * N + u0 * B.cells_per_unit;
+      FV_CK(cudaMemcpyAsync(Uh + off, Ud + off, sizeof(double) * (u1 - u0) * B.cells_per_unit,
+                            cudaMemcpyDeviceToHost, c->copy_stream));
     }
   }
-  FV_CK(cudaEventRecord(c->band_events[nb], c->copy_stream));
-  FV_CK(cudaStreamWaitEvent(c->stream, c->band_events[nb], 0));
+  FV_CK(cudaEventRecord(c->band_events[B.nb], c->copy_stream));
+  FV_CK(cudaStreamWaitEvent(c->stream, c->band_events[B.nb], 0));
   return FV_OK;
 }
 
@@ -1052,9 +1163,11 @@ int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
   bool hostU;
   if (where(c, U, &hostU)) return FV_EINVAL;
   double *Ud = U;
+  // a host state's first step overlaps its stage 1 with the copy in
+  const bool overlap = hostU && c->ngrids == 1 && nsteps > 0 && overlap_first_stage(c);
   if (hostU) {
     if ((r = ensure_staging(c))) return r;
-    FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyHostToDevice, c->stream));
+    if (!overlap) FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyHostToDevice, c->stream));
     Ud = c->stage_in;
   }
   if (c->ngrids > 1) {
@@ -1101,17 +1214,37 @@ int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
     remember_graph(c, GraphEntry{Ud, dbits, steps, exec});
     (pass == 0 ? gK : g1) = exec;
   }
-  // on a host state the last step runs outside the graphs, overlapping its
-  // copy back with the last stage kernel (fused kernels: they run by tile rows)
-  const bool banded = hostU && c->launch.mode == FV_FUSED;
-  for (int left = banded ? nsteps - 1 : nsteps; left > 0;) {
-    const int steps = left >= K ? K : 1;
-    FV_CK(cudaGraphLaunch(steps == K ? gK : g1, c->stream));
-    left -= steps;
+  // On a host state the first step (overlapping its stage 1 with the copy
+  // in) and the last step (its stage 3 writing to the host, or overlapping
+  // its copy back: fused kernels, they run by tile rows) run outside the
+  // graphs.
+  const bool to_host = hostU && c->launch.mode == FV_FUSED;
+  const unsigned long long *sm = cfl ? c->smax : nullptr;
+  int left = nsteps;
+  bool copied_back = false;
+  if (overlap) {
+    if ((r = first_stage_from_host(c, U, Ud, dt_fixed, cfl))) return r;
+    if ((r = stage(c, MODE_STAGE2, 1, c->U1, Ud, c->U2, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
+    if (nsteps == 1) {
+      if ((r = last_stage_to_host(c, Ud, U, sm, dt_fixed))) return r;
+      copied_back = true;
+    } else if ((r = stage(c, MODE_STAGE3, 2, c->U2, Ud, Ud, sm, dt_fixed, nullptr, c->t_acc, c->stream))) {
+      return r;
+    }
+    --left;
   }
-  if (hostU) {
-    if (banded && nsteps > 0) {
-      if ((r = last_step_to_host(c, Ud, U, dt_fixed, cfl))) return r;
+  for (int l = (to_host && left > 0) ? left - 1 : left; l > 0;) {
+    const int steps = l >= K ? K : 1;
+    FV_CK(cudaGraphLaunch(steps == K ? gK : g1, c->stream));
+    l -= steps;
+  }
+  if (hostU && !copied_back) {
+    if (to_host && left > 0) {
+      // the last step: CFL reduction and stages 1-2 as usual, then stage 3 to the host
+      if (cfl && (r = dt_launch(c, Ud, c->stream))) return r;
+      if ((r = stage(c, MODE_STAGE1, 0, Ud, Ud, c->U1, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
+      if ((r = stage(c, MODE_STAGE2, 1, c->U1, Ud, c->U2, sm, dt_fixed, nullptr, nullptr, c->stream))) return r;
+      if ((r = last_stage_to_host(c, Ud, U, sm, dt_fixed))) return r;
     } else {
       FV_CK(cudaMemcpyAsync(U, Ud, c->state_bytes, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -1212,7 +1345,10 @@ void fv_destroy(fv_ctx *c) {
   if (c->stage_out) cudaFree(c->stage_out);
   if (c->chunk_hi) cudaFree(c->chunk_hi);
   for (cudaEvent_t e : c->band_events) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->h2d_events) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->fd) cudaFree(c->fd);
   if (c->smax) cudaFree(c->smax);  // start of the scratch block
   if (c->norm_part) cudaFree(c->norm_part);
   if (c->X1) cudaFree(c->X1);

@@ -23,7 +23,8 @@ enum StageMode : int {
   MODE_RESIDUAL = 0,  // out = R_h (Eq. (5), face areas included)
   MODE_STAGE1 = 1,    // out = Us + dt L(Us)
   MODE_STAGE2 = 2,    // out = 3/4 Un + 1/4 (Us + dt L(Us))
-  MODE_STAGE3 = 3     // out = 1/3 Un + 2/3 (Us + dt L(Us))
+  MODE_STAGE3 = 3,    // out = 1/3 Un + 2/3 (Us + dt L(Us))
+  MODE_FLUXDIFF = 4   // fd[d] = the axis-d flux differences F_{k+1/2} - F_{k-1/2} (no face areas)
 };
 
 struct StageArgs {
@@ -56,6 +57,7 @@ struct StageArgs {
   double dt_fixed;     // step when smax is null
   double *t_acc;       // stage 3: simulated time accumulator (one thread adds dt), or null
   unsigned *flags;     // device flags (FLAG_*)
+  double *fd;          // flux-difference mode: [dim][nvar][cells] output
 };
 
 struct DtArgs {
@@ -173,6 +175,9 @@ cudaError_t set_march_attributes(size_t smem_optin);
 cudaError_t launch_stage(int dim, int mode, const CUtensorMap *tmap, const StageArgs &a, int threads,
                          cudaStream_t st);
 cudaError_t launch_dt(const DtArgs &a, int blocks, int threads, cudaStream_t st);
+// SSP-RK3 stage 1 from the per-axis flux differences of the flux-difference
+// mode (a.fd): a.out = a.Us + dt L(a.Us), bit for bit the fused stage-1 kernel.
+cudaError_t launch_stage1_from_fd(int dim, const StageArgs &a, cudaStream_t st);
 cudaError_t launch_dt_finalize(const unsigned long long *smax, double cfl, double *out, cudaStream_t st);
 cudaError_t launch_norm_finalize(const double *part, int nparts, int nvar, double *out, cudaStream_t st);
 cudaError_t launch_debug_math(const double *x, double *o1, double *o2, long n, cudaStream_t st);

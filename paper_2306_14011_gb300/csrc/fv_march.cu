@@ -344,7 +344,8 @@ cudaError_t launch_march_lim(int mode, const CUtensorMap *tmap, const StageArgs 
     case MODE_RESIDUAL: march_kernel<MODE_RESIDUAL, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
     case MODE_STAGE1: march_kernel<MODE_STAGE1, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
     case MODE_STAGE2: march_kernel<MODE_STAGE2, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
-    default: march_kernel<MODE_STAGE3, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_STAGE3: march_kernel<MODE_STAGE3, LIM><<<grid, block, smem, st>>>(*tmap, a); break;
+    default: return cudaErrorInvalidValue;  // the flux-difference mode runs on box tiles only
   }
   return cudaGetLastError();
 }

@@ -179,6 +179,49 @@ cudaError_t launch_debug_wait(int kind, unsigned long long limit_ns, unsigned *w
   return cudaGetLastError();
 }
 
+// Stage 1 from the flux differences dF_d of every axis: the fused stage-1
+// kernel's accumulation, with its operands formed as that kernel forms them
+// (dt by one division, the axis scales -w dt / dx_d with w = 1, the start
+// value U or fma(dt, S, U)) and added in its axis order, so both give the
+// same bits.  Elementwise and coalesced; HBM-bound.
+template <int DIM>
+__global__ void __launch_bounds__(256) stage1_from_fd_kernel(const StageArgs a) {
+  constexpr int NV = DIM + 2;
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+  const double w = 1.0;
+  const double dt = a.smax ? a.cfl / __longlong_as_double((long long)*a.smax) : a.dt_fixed;
+  double coef[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) coef[d] = -w * dt * a.inv_h[d];
+  const double src = w * dt;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double r = a.Us[v * N + i];
+      if (a.S) r = fma(src, a.S[v * N + i], r);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) r = fma(coef[d], a.fd[((long long)d * NV + v) * N + i], r);
+      a.out[v * N + i] = r;
+    }
+  }
+}
+
+cudaError_t launch_stage1_from_fd(int dim, const StageArgs &a, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+  long long blocks = (N + 255) / 256;
+  if (blocks > 8ll * sms) blocks = 8ll * sms;  // 2048 threads per SM, grid-stride beyond
+  if (blocks < 1) blocks = 1;
+  if (dim == 2)
+    stage1_from_fd_kernel<2><<<(unsigned)blocks, 256, 0, st>>>(a);
+  else
+    stage1_from_fd_kernel<3><<<(unsigned)blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dt(const DtArgs &a, int blocks, int threads, cudaStream_t st) {
   if (a.dim == 2) {
     if (a.bounded) dt_bound_kernel<2><<<blocks, threads, 0, st>>>(a);

@@ -283,14 +283,16 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
     const int flo = (k * fe1 + j) * fe0 + i;
     long long gi = 0;
     int lc = 0;
-    if (D == 0 && (MODE != MODE_RESIDUAL || a.S)) {
+    if (D == 0 && MODE != MODE_FLUXDIFF && (MODE != MODE_RESIDUAL || a.S)) {
       gi = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
       lc = (((DIM == 3) ? k + 2 : 0) * G.BY + (j + 2)) * G.BX + (i + 2);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const double dF = F[v * G.fmax + flo + fstride] - F[v * G.fmax + flo];
-      if (D == 0) {
+      if (MODE == MODE_FLUXDIFF) {  // this axis's differences alone, written out after the pass
+        R[v * G.cells + c] = dF;
+      } else if (D == 0) {
         if (MODE == MODE_RESIDUAL && !a.S)
           R[v * G.cells + c] = coef * dF;
         else  // stages 2 and 3: R holds U^n, copied in by prefetch_un
@@ -304,6 +306,26 @@ __device__ __forceinline__ void face_pass(const double *__restrict__ tile, doubl
     }
   }
   __syncthreads();
+}
+
+// The tile's cells of the accumulator R into the SoA array dst (the
+// flux-difference mode's per-axis output).  R is not written again before the
+// next face pass's barrier, so no barrier is needed here.
+template <int DIM>
+__device__ __forceinline__ void store_cells(const double *R, double *dst, const StageArgs &a, const int o[3],
+                                            const int ext[3], const TileGeom &G) {
+  constexpr int NV = DIM + 2;
+  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+  const int ncell = ext[0] * ext[1] * ext[2];
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int i = c % ext[0];
+    const int rr = c / ext[0];
+    const int j = rr % ext[1];
+    const int k = rr / ext[1];
+    const long long gi = ((long long)(o[2] + k) * a.n[1] + (o[1] + j)) * a.n[0] + (o[0] + i);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * N + gi] = R[v * G.cells + c];
+  }
 }
 
 // Stages 2 and 3: U^n of the tile's cells into the accumulator R, with
@@ -408,8 +430,14 @@ __device__ __forceinline__ bool tile_work(const CUtensorMap *tmap, const StageAr
   }
   const double dt = s_coef[0];
   face_pass<DIM, 0, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[1], s_coef[4]);
+  if (MODE == MODE_FLUXDIFF) store_cells<DIM>(R, a.fd, a, o, ext, G);
   face_pass<DIM, 1, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[2], s_coef[4]);
-  if constexpr (DIM == 3) face_pass<DIM, 2, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[3], s_coef[4]);
+  if (MODE == MODE_FLUXDIFF) store_cells<DIM>(R, a.fd + (long long)NV * N, a, o, ext, G);
+  if constexpr (DIM == 3) {
+    face_pass<DIM, 2, LIM, MODE>(tile, F, R, a, o, ext, G, s_coef[3], s_coef[4]);
+    if (MODE == MODE_FLUXDIFF) store_cells<DIM>(R, a.fd + 2ll * NV * N, a, o, ext, G);
+  }
+  if (MODE == MODE_FLUXDIFF) return true;
 
   // ---- 4. epilogue
   const int ncell = ext[0] * ext[1] * ext[2];
@@ -510,7 +538,8 @@ cudaError_t launch_stage_lim(int mode, const CUtensorMap *tmap, const StageArgs 
     case MODE_RESIDUAL: stage_kernel<DIM, MODE_RESIDUAL, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
     case MODE_STAGE1: stage_kernel<DIM, MODE_STAGE1, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
     case MODE_STAGE2: stage_kernel<DIM, MODE_STAGE2, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
-    default: stage_kernel<DIM, MODE_STAGE3, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
+    case MODE_STAGE3: stage_kernel<DIM, MODE_STAGE3, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
+    default: stage_kernel<DIM, MODE_FLUXDIFF, LIM, MAXT><<<grid, block, smem, st>>>(*tmap, a); break;
   }
   return cudaGetLastError();
 }
@@ -529,11 +558,12 @@ cudaError_t launch_stage_dim(int mode, const CUtensorMap *tmap, const StageArgs 
 template <int DIM, int LIM, int MAXT>
 cudaError_t set_stage_attributes_lim(size_t smem_optin) {
   cudaError_t e = cudaSuccess;
-  const void *k[4] = {(const void *)stage_kernel<DIM, MODE_RESIDUAL, LIM, MAXT>,
+  const void *k[5] = {(const void *)stage_kernel<DIM, MODE_RESIDUAL, LIM, MAXT>,
                       (const void *)stage_kernel<DIM, MODE_STAGE1, LIM, MAXT>,
                       (const void *)stage_kernel<DIM, MODE_STAGE2, LIM, MAXT>,
-                      (const void *)stage_kernel<DIM, MODE_STAGE3, LIM, MAXT>};
-  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+                      (const void *)stage_kernel<DIM, MODE_STAGE3, LIM, MAXT>,
+                      (const void *)stage_kernel<DIM, MODE_FLUXDIFF, LIM, MAXT>};
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, k[i]);
     if (e == cudaSuccess)
