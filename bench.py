@@ -66,14 +66,14 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # dram__bytes_write.sum, full 4096^2 launches, mean of the three stages of one
 # step), valid for the kernel sources whose hash and the launch shape recorded
 # with it; null otherwise.
-STAGE_TRAFFIC = {"bytes": 1.3892e9, "source_hash": "68847fbb2e4d39b5", "tile": [64, 16, 1], "threads": 192}
+STAGE_TRAFFIC = {"bytes": 1.3891e9, "source_hash": "b015986973ece0c2", "tile": [64, 16, 1], "threads": 192}
 # FP64 instructions the fused stage kernels execute per cell and stage (ncu
 # sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on, mean of the three
 # stages at 2048^2 / 192^3), for the kernel sources with this hash; and the
 # FP64 products evaluated on the integer pipe instead: 29 per face in 2D and 32
 # in 3D (the Roe flux's products), times the faces per cell of the default
 # tiles (2.078 for 64x16, 3.375 for 8x8x8).
-STAGE_FP64_INST = {"2d": 114.3, "3d": 231.2, "source_hash": "68847fbb2e4d39b5"}
+STAGE_FP64_INST = {"2d": 114.3, "3d": 231.2, "source_hash": "b015986973ece0c2"}
 INT_PIPE_PRODUCTS = {"2d": 60.3, "3d": 108.0}
 
 
