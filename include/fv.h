@@ -214,7 +214,15 @@ int fv_rk_step(fv_ctx *ctx, double *U, double dt, double *dt_used);
  * NULL (asynchronous) or a host pointer receiving the simulated time -- one
  * double per grid (ngrids of them) -- (the call waits and reports device-side
  * flags).  Batched contexts: U is the packed state, and a grid barrier that
- * waits longer than 2 s ends the kernel with FV_ETIMEOUT. */
+ * waits longer than 2 s ends the kernel with FV_ETIMEOUT.
+ * A host state U (single-grid contexts, fused kernels, box-tiled stage 1)
+ * gives the same bits as a device state, with the copies overlapped: the
+ * first step's stage 1 computes its flux differences band by band as the
+ * state arrives and forms U1 from them once the CFL step is known
+ * (allocates, on first use, a device buffer of dim states for them, plus a
+ * second stream), and on page-locked host memory mapped into the device's
+ * address space the last stage writes the result to U directly (pageable
+ * memory: copied back band by band). */
 int fv_run(fv_ctx *ctx, double *U, int nsteps, double dt_fixed, double *t_out);
 
 /* Discrete adjoint (vector-Jacobian products), FP64, single-grid contexts.
