@@ -220,7 +220,8 @@ int fv_rk_step(fv_ctx *ctx, double *U, double dt, double *dt_used);
  * first step's stage 1 computes its flux differences band by band as the
  * state arrives and forms U1 from them once the CFL step is known
  * (allocates, on first use, a device buffer of dim states for them, plus a
- * second stream), and on page-locked host memory mapped into the device's
+ * second stream; without that memory the state is copied in whole first,
+ * with the same result), and on page-locked host memory mapped into the device's
  * address space the last stage writes the result to U directly (pageable
  * memory: copied back band by band). */
 int fv_run(fv_ctx *ctx, double *U, int nsteps, double dt_fixed, double *t_out);

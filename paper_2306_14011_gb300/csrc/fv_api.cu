@@ -1057,7 +1057,7 @@ int first_stage_from_host(fv_ctx *c, const double *Uh, double *Ud, double dt_fix
   const int ramp[6] = {1, 1, 1, 2, 4, 8};
   for (int q = 0; rb.back() < B.rows; ++q) rb.push_back(std::min(B.rows, rb.back() + (q < 6 ? ramp[q] : 16)));
   const int nb = (int)rb.size() - 1;
-  if (!c->fd) FV_CK(cudaMalloc(&c->fd, sizeof(double) * (size_t)g.dim * c->state_bytes / sizeof(double)));
+  if (!c->fd) return FV_EINVAL;  // allocated by the caller's check
   if (!c->copy_stream) FV_CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
   if (!c->aux_stream) FV_CK(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
   int r;
@@ -1163,8 +1163,15 @@ int fv_run(fv_ctx *c, double *U, int nsteps, double dt_fixed, double *t_out) {
   bool hostU;
   if (where(c, U, &hostU)) return FV_EINVAL;
   double *Ud = U;
-  // a host state's first step overlaps its stage 1 with the copy in
-  const bool overlap = hostU && c->ngrids == 1 && nsteps > 0 && overlap_first_stage(c);
+  // a host state's first step overlaps its stage 1 with the copy in (when
+  // the buffer of its flux differences can be had; else the copy comes first)
+  bool overlap = hostU && c->ngrids == 1 && nsteps > 0 && overlap_first_stage(c);
+  if (overlap && !c->fd &&
+      cudaMalloc(&c->fd, sizeof(double) * (size_t)c->grid.dim * c->state_bytes / sizeof(double)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    c->fd = nullptr;
+    overlap = false;
+  }
   if (hostU) {
     if ((r = ensure_staging(c))) return r;
     if (!overlap) FV_CK(cudaMemcpyAsync(c->stage_in, U, c->state_bytes, cudaMemcpyHostToDevice, c->stream));
