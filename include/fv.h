@@ -174,7 +174,9 @@ int fv_init(fv_ctx **out, const fv_grid *grids, int ngrids, const fv_scheme *s, 
  * 256-byte boundaries. */
 int fv_layout(const fv_ctx *ctx, long long *offsets, int ngrids);
 
-/* Replace / read the launch configuration (validated against the device). */
+/* Replace / read the launch configuration (validated against the device).
+ * fv_set_launch waits for the context's queued work and drops its captured
+ * graphs. */
 int fv_set_launch(fv_ctx *ctx, const fv_launch *l);
 int fv_get_launch(const fv_ctx *ctx, fv_launch *l);
 

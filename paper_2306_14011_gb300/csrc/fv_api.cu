@@ -481,6 +481,8 @@ int set_attributes(fv_ctx *c) {
   return FV_OK;
 }
 
+// Callers make sure no launch of the graph is still queued when it owns
+// device memory (cudaFree also waits for the device).
 void destroy_graph(GraphEntry &g) {
   cudaGraphExecDestroy(g.exec);
   if (g.aux) cudaFree(g.aux);
@@ -499,6 +501,7 @@ void remember_graph(fv_ctx *c, const GraphEntry &e) {
   // graph of e.U that it is about to launch)
   for (size_t i = 0; c->graphs.size() >= kMaxGraphs && i < c->graphs.size();) {
     if (c->graphs[i].U != e.U) {
+      if (c->graphs[i].aux) cudaStreamSynchronize(c->stream);  // its last launch may be queued
       destroy_graph(c->graphs[i]);
       c->graphs.erase(c->graphs.begin() + i);
     } else {
@@ -872,6 +875,8 @@ int fv_set_launch(fv_ctx *c, const fv_launch *l) {
   if (r) return r;
   if (c->ngrids > 1 && l->mode != FV_FUSED) return FV_EUNSUPPORTED;
   if (l->mode == FV_SPLIT && (r = ensure_split(c))) return r;
+  // queued work may still read the graphs' tile-load maps and the batch tables
+  FV_CK(cudaStreamSynchronize(c->stream));
   c->launch = *l;
   drop_graphs(c);
   if ((r = set_attributes(c))) return r;
