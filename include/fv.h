@@ -244,6 +244,25 @@ int fv_run(fv_ctx *ctx, double *U, int nsteps, double dt_fixed, double *t_out);
 enum { FV_VJP_RESIDUAL = 0, FV_VJP_RKSTEP = 1 };
 int fv_adjoint_vjp(fv_ctx *ctx, int what, const double *U, const double *lambda, double dt, double *out);
 
+/* One SSP-RK3 step of fv_rk_step at the fixed step dt > 0, in place on the
+ * device state U, that also writes its two stage states (Eq. (4)):
+ *   U1 = U + dt L(U),  U2 = 3/4 U + 1/4 (U1 + dt L(U1))
+ * into caller-owned device arrays U1, U2 of the state's size (distinct from
+ * U and from each other).  U after the call is bit for bit fv_rk_step's.  For
+ * the discrete adjoint of a run: with the stage states kept, the step's VJP
+ * (fv_adjoint_vjp_stages) does not recompute them.  Single-grid contexts
+ * (FV_EUNSUPPORTED otherwise); FV_EINVAL for dt <= 0, host pointers or
+ * aliased arrays.  Stream-ordered; returns without waiting. */
+int fv_rk_step_stages(fv_ctx *ctx, double *U, double dt, double *U1, double *U2);
+
+/* The FV_VJP_RKSTEP product of fv_adjoint_vjp, out = (dU^{n+1}/dU^n)^T
+ * lambda at the fixed step dt > 0, from the step's stage states U1, U2 as
+ * fv_rk_step_stages wrote them for the same U and dt (not recomputed): the
+ * same bits as fv_adjoint_vjp.  Device arrays of the state's size; out must
+ * not alias any input.  Same support and errors as fv_adjoint_vjp. */
+int fv_adjoint_vjp_stages(fv_ctx *ctx, const double *U, const double *U1, const double *U2, const double *lambda,
+                          double dt, double *out);
+
 /* Wait for all work of the context and report (then clear) device-side
  * flags: FV_ENONPHYSICAL, FV_ETIMEOUT, or FV_OK. */
 int fv_sync(fv_ctx *ctx);

@@ -1319,6 +1319,23 @@ int adjoint(fv_ctx *c, const double *U, const double *lam, double *out, double w
 
 }  // namespace
 
+namespace {
+
+// The reverse of one SSP-RK3 step at fixed dt, given its stage states U1, U2:
+// three residual VJPs with the transposed stage combinations.
+int rk_step_reverse(fv_ctx *c, const double *U, const double *U1, const double *U2, const double *lam, double dt,
+                    double *out) {
+  int r;
+  // X2 = dJ/dU2 = 2/3 lam + 2/3 dt (dL/dU2)^T lam
+  if ((r = adjoint(c, U2, lam, c->X2, (2.0 / 3.0) * dt, lam, 2.0 / 3.0, nullptr, 0.0, nullptr, 0.0))) return r;
+  // X1 = dJ/dU1 = 1/4 X2 + 1/4 dt (dL/dU1)^T X2
+  if ((r = adjoint(c, U1, c->X2, c->X1, 0.25 * dt, c->X2, 0.25, nullptr, 0.0, nullptr, 0.0))) return r;
+  // out = 1/3 lam + 3/4 X2 + X1 + dt (dL/dU)^T X1
+  return adjoint(c, U, c->X1, out, dt, lam, 1.0 / 3.0, c->X2, 0.75, c->X1, 1.0);
+}
+
+}  // namespace
+
 extern "C" int fv_adjoint_vjp(fv_ctx *c, int what, const double *U, const double *lam, double dt, double *out) {
   if (!c || !U || !lam || !out || out == U || out == lam) return FV_EINVAL;
   if (c->ngrids > 1 || c->scheme.limiter != FV_LIM_MINMOD || c->scheme.recon != FV_RECON_CONSERVED)
@@ -1334,12 +1351,35 @@ extern "C" int fv_adjoint_vjp(fv_ctx *c, int what, const double *U, const double
   // forward stage states of the step: U1 = U + dt L(U), U2 = 3/4 U + 1/4 (U1 + dt L(U1))
   if ((r = stage(c, MODE_STAGE1, 0, U, U, c->U1, nullptr, dt, nullptr, nullptr, c->stream))) return r;
   if ((r = stage(c, MODE_STAGE2, 1, c->U1, U, c->U2, nullptr, dt, nullptr, nullptr, c->stream))) return r;
-  // reverse: X2 = dJ/dU2 = 2/3 lam + 2/3 dt (dL/dU2)^T lam
-  if ((r = adjoint(c, c->U2, lam, c->X2, (2.0 / 3.0) * dt, lam, 2.0 / 3.0, nullptr, 0.0, nullptr, 0.0))) return r;
-  // X1 = dJ/dU1 = 1/4 X2 + 1/4 dt (dL/dU1)^T X2
-  if ((r = adjoint(c, c->U1, c->X2, c->X1, 0.25 * dt, c->X2, 0.25, nullptr, 0.0, nullptr, 0.0))) return r;
-  // out = 1/3 lam + 3/4 X2 + X1 + dt (dL/dU)^T X1
-  return adjoint(c, U, c->X1, out, dt, lam, 1.0 / 3.0, c->X2, 0.75, c->X1, 1.0);
+  return rk_step_reverse(c, U, c->U1, c->U2, lam, dt, out);
+}
+
+int fv_rk_step_stages(fv_ctx *c, double *U, double dt, double *U1, double *U2) {
+  if (!c || !U || !U1 || !U2 || U1 == U || U2 == U || U1 == U2 || !(dt > 0.0)) return FV_EINVAL;
+  if (c->ngrids > 1) return FV_EUNSUPPORTED;
+  if (pointer_kind(U, c->device) != PTR_DEVICE || pointer_kind(U1, c->device) != PTR_DEVICE ||
+      pointer_kind(U2, c->device) != PTR_DEVICE)
+    return FV_EINVAL;
+  // the stage launches of fv_rk_step at a fixed step, into the caller's stage arrays
+  int r;
+  if ((r = stage(c, MODE_STAGE1, 0, U, U, U1, nullptr, dt, nullptr, nullptr, c->stream))) return r;
+  if ((r = stage(c, MODE_STAGE2, 1, U1, U, U2, nullptr, dt, nullptr, nullptr, c->stream))) return r;
+  return stage(c, MODE_STAGE3, 2, U2, U, U, nullptr, dt, nullptr, nullptr, c->stream);
+}
+
+int fv_adjoint_vjp_stages(fv_ctx *c, const double *U, const double *U1, const double *U2, const double *lam,
+                          double dt, double *out) {
+  if (!c || !U || !U1 || !U2 || !lam || !out || out == U || out == lam || out == U1 || out == U2 || !(dt > 0.0))
+    return FV_EINVAL;
+  if (c->ngrids > 1 || c->scheme.limiter != FV_LIM_MINMOD || c->scheme.recon != FV_RECON_CONSERVED)
+    return FV_EUNSUPPORTED;
+  if (pointer_kind(U, c->device) != PTR_DEVICE || pointer_kind(U1, c->device) != PTR_DEVICE ||
+      pointer_kind(U2, c->device) != PTR_DEVICE || pointer_kind(lam, c->device) != PTR_DEVICE ||
+      pointer_kind(out, c->device) != PTR_DEVICE)
+    return FV_EINVAL;
+  if (!c->X1) FV_CK(cudaMalloc(&c->X1, c->state_bytes));
+  if (!c->X2) FV_CK(cudaMalloc(&c->X2, c->state_bytes));
+  return rk_step_reverse(c, U, U1, U2, lam, dt, out);
 }
 
 int fv_sync(fv_ctx *c) {

@@ -129,6 +129,10 @@ def load() -> C.CDLL:
         L.fv_layout.restype = C.c_int
         L.fv_adjoint_vjp.argtypes = [_VP, C.c_int, _VP, _VP, C.c_double, _VP]
         L.fv_adjoint_vjp.restype = C.c_int
+        L.fv_rk_step_stages.argtypes = [_VP, _VP, C.c_double, _VP, _VP]
+        L.fv_rk_step_stages.restype = C.c_int
+        L.fv_adjoint_vjp_stages.argtypes = [_VP, _VP, _VP, _VP, _VP, C.c_double, _VP]
+        L.fv_adjoint_vjp_stages.restype = C.c_int
         for name in ("fv_default_launch", "fv_init", "fv_set_launch", "fv_get_launch", "fv_residual",
                      "fv_time_step", "fv_rk_step", "fv_run", "fv_sync", "fv_debug_math"):
             getattr(L, name).restype = C.c_int
@@ -389,6 +393,19 @@ def fv_adjoint_vjp(ctx: int, what: int, U, lam, dt: float, out):
     _check(load().fv_adjoint_vjp(ctx, what, _ptr(U), _ptr(lam), float(dt), _ptr(out)), "fv_adjoint_vjp")
 
 
+def fv_rk_step_stages(ctx: int, U, dt: float, U1, U2):
+    """One fixed-dt SSP-RK3 step in place on U that also writes its stage
+    states U1, U2 (device tensors of U's shape)."""
+    _check(load().fv_rk_step_stages(ctx, _ptr(U), float(dt), _ptr(U1), _ptr(U2)), "fv_rk_step_stages")
+
+
+def fv_adjoint_vjp_stages(ctx: int, U, U1, U2, lam, dt: float, out):
+    """out = (dU_{n+1}/dU_n)^T lam for one fixed-dt SSP-RK3 step from its
+    stage states U1, U2 (as fv_rk_step_stages wrote them).  Device tensors."""
+    _check(load().fv_adjoint_vjp_stages(ctx, _ptr(U), _ptr(U1), _ptr(U2), _ptr(lam), float(dt), _ptr(out)),
+           "fv_adjoint_vjp_stages")
+
+
 def fv_debug_bits(op: int, x, out, y=None, stream=None):
     """out = op(x[, y]) with the kernels' integer-pipe helpers (see fv.h)."""
     _check(load().fv_debug_bits(int(op), _ptr(x), None if y is None else _ptr(y), _ptr(out), x.numel(),
@@ -506,6 +523,19 @@ class Solver:
         """(dU_{n+1}/dU_n)^T lam for one fixed-dt SSP-RK3 step taken from U."""
         out = torch_empty_like(U) if out is None else out
         fv_adjoint_vjp(self.ctx, FV_VJP_RKSTEP, U, lam, dt, out)
+        return out
+
+    def rk_step_stages(self, U, dt: float, U1, U2):
+        """One fixed-dt SSP-RK3 step in place on U, also writing its stage
+        states into U1 and U2."""
+        self._chk(U)
+        fv_rk_step_stages(self.ctx, U, dt, U1, U2)
+
+    def rk_step_vjp_stages(self, U, U1, U2, lam, dt: float, out=None):
+        """rk_step_vjp from the step's stage states (as rk_step_stages wrote
+        them): the same values without recomputing the stages."""
+        out = torch_empty_like(U) if out is None else out
+        fv_adjoint_vjp_stages(self.ctx, U, U1, U2, lam, dt, out)
         return out
 
     def set_source(self, S):

@@ -189,6 +189,36 @@ def test_unrolled_gradient_matches_oracle_forward_mode():
     assert abs(lhs - rhs) <= 1e-11 * np.sum(np.abs(w * dUN))
 
 
+def test_stage_states_kept_give_the_same_step_and_gradient_bitwise():
+    """fv_rk_step_stages advances U exactly as fv_rk_step and writes the
+    step's stage states; the VJP from them equals the VJP that recomputes
+    them; the checkpointed gradient with stage states kept equals the one
+    without, bit for bit."""
+    from paper_2306_14011_gb300.autograd import FvRunFunction
+    g, U = I.isentropic_vortex(64, seed=2)
+    dt = O.time_step(g, U)
+    rng = np.random.default_rng(4)
+    lam = dev(rng.normal(size=U.shape))
+    w = dev(rng.normal(size=U.shape))
+    with fv.Solver(g) as s:
+        A, B = dev(U), dev(U)
+        s.rk_step(A, dt)
+        U1, U2 = torch.empty_like(B), torch.empty_like(B)
+        s.rk_step_stages(B, dt, U1, U2)
+        assert torch.equal(A, B)
+        assert torch.equal(s.rk_step_vjp_stages(dev(U), U1, U2, lam, dt), s.rk_step_vjp(dev(U), lam, dt))
+        grads = []
+        for keep in (True, False):
+            U0 = dev(U).requires_grad_()
+            (FvRunFunction.apply(U0, s, 23, dt, 5, keep) * w).sum().backward()
+            grads.append(U0.grad.clone())
+        assert torch.equal(grads[0], grads[1])
+        with pytest.raises(fv.FvError):
+            s.rk_step_stages(A, dt, A, U2)  # aliased stage array
+        with pytest.raises(fv.FvError):
+            s.rk_step_stages(A, 0.0, U1, U2)  # needs a fixed step
+
+
 def _config5(eps, every, steps=400, n=1024, directions=16, h=1e-6, with_magnitudes=False):
     """Gradient of the kinetic energy after `steps` fixed-dt SSP-RK3 steps of
     the n x n periodic isentropic vortex w.r.t. U0 (CFL step of U0, held),
