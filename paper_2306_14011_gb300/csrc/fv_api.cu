@@ -67,7 +67,7 @@ PointerAttributeFn pointer_attribute_fn() {
 // The device address of host memory [p, p + bytes) when the whole range lies
 // in one page-locked allocation mapped into the current device's address
 // space, so that kernels may store to it directly; nullptr otherwise
-// (pageable memory, or a range the driver cannot vouch for).
+// (pageable memory, or a range the CUDA driver does not report as one allocation).
 double *mapped_host_range(double *p, size_t bytes) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
